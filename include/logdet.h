@@ -1,0 +1,136 @@
+/*
+ * liblogdet: sign(det A) and log|det A| by Salem-Said matrix condensation with
+ * max-abs pivoting inside the pivot row (Dong, Barnett, Dhall, "Parallel Matrix
+ * Condensation for Calculating Log-Determinant of Large Matrix").
+ *
+ * One condensation step (Eqs. (2)-(3), Sec. 2.2-2.4, Fig. 6 with one process):
+ *   k   = first active row (the pivot row),
+ *   l   = argmax_j |a_kj| over the m active columns, ties to the smallest
+ *         original column label (Sec. 2.2),
+ *   r   = row k divided by p = a_kl (the pivot factored out of the ROW, Sec. 2.3),
+ *   column l is swapped with the last active column (Sec. 2.4, Fig. 5) and the
+ *   swap parity goes into the sign,
+ *   a_ij <- a_ij - a_il * r_j for the remaining rows and columns (Eq. (2) with a
+ *   unit pivot), one fused multiply-add per element,
+ *   log|det A| += log|p|, sign(det A) *= sgn(p) * (-1)^(m+1) * (l != m-1 ? -1 : 1).
+ *
+ * Conventions (all entry points):
+ *   - Matrices are row-major with a leading dimension (elements between row
+ *     starts) lda >= n. Inputs are never modified.
+ *   - Every function returns an ld_status; nothing traps or aborts. Device-side
+ *     errors are reported through the status of the call that observes them.
+ *   - n == 0 gives sign 1, logabs 0. An all-zero pivot row gives sign 0 and
+ *     logabs -inf with LD_OK (the matrix is singular in the arithmetic used).
+ *     A NaN in any pivot row gives NaN for both.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued on it; temporary device memory is stream-ordered
+ *     (cudaMallocAsync / cudaFreeAsync) and owned by the library.
+ *   - The caller owns every buffer passed in. The library frees none of them.
+ */
+#ifndef LIBLOGDET_H_
+#define LIBLOGDET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage and arithmetic of one sweep. */
+typedef enum {
+  LD_F64_PLAIN = 0,   /* FP64 storage, one rank-1 update per pivot (Eq. (2)) */
+  LD_F64_BLOCKED = 1, /* FP64 storage, panels of b pivots + FP64 rank-b update */
+  LD_F32_PLAIN = 2,   /* FP32 storage, one rank-1 update per pivot */
+  LD_F32_TF32 = 3,    /* FP32 storage, panels + TF32 tensor-core rank-b update */
+  LD_F32_3XTF32 = 4,  /* FP32 storage, panels + split-TF32 (hi*hi+hi*lo+lo*hi) */
+  LD_F32_BF16X3 = 5   /* FP32 storage, panels + split-BF16 (hi*hi+hi*lo+lo*hi) */
+} ld_mode;
+
+/* Element type of an input matrix. */
+typedef enum { LD_DTYPE_F64 = 0, LD_DTYPE_F32 = 1 } ld_dtype;
+
+typedef enum {
+  LD_OK = 0,
+  LD_ERR_INVALID_ARG = 1, /* bad size, leading dimension, pointer or enum */
+  LD_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve */
+  LD_ERR_ALLOC = 3,       /* device memory allocation failed */
+  LD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  LD_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} ld_status;
+
+/*
+ * ld_logdet - sign and log|det| of one n x n matrix (Eqs. (2)-(3), Sec. 2.2-2.4).
+ *   A        device pointer, row-major, element type a_dtype, leading dim lda
+ *   mode     storage/arithmetic of the sweep (see ld_mode)
+ *   sign     out: +1, -1, 0 or NaN. Host or device pointer (detected with
+ *            cudaPointerGetAttributes); a host pointer makes the call wait for
+ *            `stream` before it returns
+ *   logabs   out: log|det A| (same pointer rules as sign)
+ * Errors: LD_ERR_INVALID_ARG for n < 0, lda < max(n,1), NULL A (n > 0) or NULL
+ * outputs, or an unknown enum; LD_ERR_ALLOC / LD_ERR_CUDA as named.
+ */
+ld_status ld_logdet(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
+                    void* stream, double* sign, double* logabs);
+
+/*
+ * ld_factors_size - bytes of the factor record that ld_logdet_factor writes for
+ * an n x n matrix in `mode` (0 for an invalid request). The record is
+ *   [0, 256)            header: int64 n, int64 ldf, int32 mode, int32 flags,
+ *                       double sign, double logabs (rest reserved)
+ *   [256, +n*ldf*es)    F: n x ldf row-major, es = 8 (F64 modes) or 4 (F32 modes)
+ *   then int32 colperm[n], int32 pivpos[n], double pivval[n] (each 256-B aligned)
+ * F holds the packed Crout factors in the swap-to-boundary layout: the column
+ * that step s eliminates sits at position n-1-s, F[s][n-1-s] = pivot p_s,
+ * F[i][n-1-s] (i > s) = multiplier c_i of step s, F[s][q] (q < n-1-s) = factored
+ * row r_s. colperm[q] = original column label at position q. pivpos[s] = position
+ * of the pivot in row s before its swap; pivval[s] = p_s (as FP64).
+ */
+size_t ld_factors_size(int64_t n, ld_mode mode);
+
+/*
+ * ld_logdet_factor - as ld_logdet, and keeps the factor record.
+ *   factors  device buffer of ld_factors_size(n, mode) bytes, 256-B aligned
+ *   sign, logabs  as ld_logdet (also stored in the record header)
+ */
+ld_status ld_logdet_factor(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
+                           void* stream, void* factors, double* sign, double* logabs);
+
+/*
+ * ld_logdet_backward - G = g * d log|det A| / dA = g * A^{-T} (Jacobi's formula)
+ * from a factor record: with A Q J = L U (Q = colperm, J = column reversal),
+ * A^{-1} = Q J U^{-1} L^{-1}.
+ *   factors  device factor record written by ld_logdet_factor (read only)
+ *   g        device pointer to one double (the incoming gradient of logabs)
+ *   grad     device output, n x ldg row-major, element type of the mode's storage
+ * The paper has no derivative; this is the chain rule applied to its output.
+ */
+ld_status ld_logdet_backward(const void* factors, const double* g, void* grad, int64_t ldg,
+                             void* stream);
+
+/*
+ * ld_logdet_batched - sign and log|det| of `count` independent matrices in one
+ * persistent launch (Sec. 1 names the per-component log-determinants of a
+ * Gaussian mixture; each matrix runs the same sweep as ld_logdet).
+ *   A_ptrs   device array of `count` device pointers (element type a_dtype)
+ *   n, lda   device arrays of `count` int64 sizes / leading dimensions
+ *   n_max    host bound on every n[i] (sizes the workspace); n[i] > n_max gives
+ *            NaN for that matrix
+ *   signs, logabs  device arrays of `count` doubles
+ * Modes: LD_F32_PLAIN and LD_F64_PLAIN. No host synchronisation; the call can
+ * be captured in a CUDA graph once its workspace exists (see ld_batched_reserve).
+ */
+ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                            const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,
+                            void* stream, double* signs, double* logabs);
+
+/* Human-readable name of a status code (static storage). */
+const char* ld_status_string(ld_status s);
+
+/* Library version, e.g. "liblogdet 0.1 sm_103a". */
+const char* ld_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBLOGDET_H_ */

@@ -1,0 +1,155 @@
+"""Seeded synthetic inputs for the condensation log-determinant.
+
+This module holds generators only: it contains none of the method's arithmetic,
+and both the oracle side and the CUDA side draw their inputs from it. All CPU
+generators use ``numpy.random.default_rng(seed)`` in FP64.
+
+Workloads (the paper times FP64 dense matrices of size 1000..8000, Sec. 3, with no
+stated distribution; these recipes stand in for its matrices):
+
+  dense_gaussian(N, seed, var)   iid N(0, var) entries
+  spd_covariance(N, seed, ...)   X^T X / m + ridge * I with X an m x N iid N(0,1) matrix
+  spd_spectrum(N, seed, lo, hi)  Q diag(lambda) Q^T, Q Haar orthogonal (QR of a
+                                 Gaussian with the sign of diag(R) folded in),
+                                 lambda log-uniform in [lo, hi]; returns the exact
+                                 sum of log(lambda) alongside
+  batched_sizes(count, seed)     sizes uniform on {32, 48, ..., 512}
+  dyadic_lu(n, seed)             integer/dyadic matrices whose whole condensation
+                                 sweep is exact in FP32, with the pivot labels and
+                                 determinant known by construction
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Named workloads (sizes and seeds of the benchmark and parity suites).
+CONFIG_1000 = dict(N=1000, seed=0, var=1.0)           # dense iid N(0,1), FP64
+CONFIG_8000 = dict(N=8000, seed=1, var=1.0 / 8000.0)  # dense iid N(0,1/N)
+CONFIG_SPD_16384 = dict(N=16384, seed=2, lo=1e-4, hi=1.0)
+CONFIG_SPD_32768 = dict(N=32768, seed=2, lo=1e-4, hi=1.0)
+CONFIG_BATCH = dict(count=4096, seed=3, ridge=1e-2)
+CONFIG_GRAD = dict(batch=256, N=1024, seed=4, lo=1e-2, hi=1.0)
+
+
+def dense_gaussian(N: int, seed: int, var: float = 1.0, rng=None) -> np.ndarray:
+    rng = np.random.default_rng(seed) if rng is None else rng
+    return rng.standard_normal((N, N)) * math.sqrt(var)
+
+
+def spd_covariance(N: int, seed: int = 0, m: int | None = None, ridge: float = 1e-3,
+                   rng=None) -> np.ndarray:
+    """X^T X / m + ridge * I, X an m x N iid N(0,1) matrix (m = 2N by default)."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    m = 2 * N if m is None else m
+    X = rng.standard_normal((m, N))
+    A = (X.T @ X) / m
+    A[np.diag_indices(N)] += ridge
+    return A
+
+
+def dense_and_spd_pair(N: int, seed: int):
+    """The two N x N matrices of one seed: iid N(0, 1/N), then from the same
+    generator X (2N x N) for X^T X / (2N) + 1e-3 I."""
+    rng = np.random.default_rng(seed)
+    A = dense_gaussian(N, seed, 1.0 / N, rng=rng)
+    S = spd_covariance(N, m=2 * N, ridge=1e-3, rng=rng)
+    return A, S
+
+
+def haar_orthogonal(N: int, rng) -> np.ndarray:
+    G = rng.standard_normal((N, N))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def spd_spectrum(N: int, seed: int, lo: float = 1e-4, hi: float = 1.0):
+    """(A, lam, exact_sum_log) with A = Q diag(lam) Q^T, lam = 10^U(log10 lo, log10 hi)."""
+    rng = np.random.default_rng(seed)
+    lam = 10.0 ** rng.uniform(math.log10(lo), math.log10(hi), size=N)
+    Q = haar_orthogonal(N, rng)
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    return A, lam, math.fsum(math.log(x) for x in lam)
+
+
+def spd_spectrum_torch(N: int, seed: int, lo: float, hi: float, device, dtype=None):
+    """GPU generator of the same recipe for sizes where a CPU QR is too slow.
+
+    Draws with a seeded ``torch.Generator`` on ``device``; returns
+    (A [FP64 on device], exact_sum_log). Only torch library calls (randn, QR,
+    matmul) are used: plumbing, not the method.
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = torch.rand(N, generator=g, device=device, dtype=torch.float64)
+    lam = 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+    G = torch.randn(N, N, generator=g, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    Q = Q * torch.sign(torch.diagonal(R))[None, :]
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    sum_log = math.fsum(float(x) for x in torch.log(lam).cpu().tolist())
+    if dtype is not None:
+        A = A.to(dtype)
+    return A, sum_log
+
+
+def dense_and_spd_pair_torch(N: int, seed: int, device):
+    """GPU generator of the iid N(0,1/N) matrix and X^T X/(2N) + 1e-3 I (FP64)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = torch.randn(N, N, generator=g, device=device, dtype=torch.float64) / math.sqrt(N)
+    X = torch.randn(2 * N, N, generator=g, device=device, dtype=torch.float64)
+    S = (X.T @ X) / (2 * N)
+    S.diagonal().add_(1e-3)
+    return A, S
+
+
+def batched_sizes(count: int = 4096, seed: int = 3) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 31, size=count) * 16 + 32
+
+
+def batched_covariances(sizes, seed: int = 3, ridge: float = 1e-2):
+    """One X^T X / (2n) + ridge * I matrix per size (X is 2n x n), one generator."""
+    rng = np.random.default_rng(seed + 1000)
+    return [spd_covariance(int(n), m=2 * int(n), ridge=ridge, rng=rng) for n in sizes]
+
+
+def dyadic_lu(n: int, seed: int, density: float = 0.3):
+    """A = (L U) P^T with exact pivots: returns (A, det, labels).
+
+    L is unit lower triangular with entries in {-1, 0, 1}; U is upper triangular
+    with diagonal +-8 and off-diagonal entries in {-1, 0, 1}; P permutes columns.
+    After t condensation steps with the first row as pivot row, the remaining
+    matrix is L[t:, t:] U[t:, t:] (permuted), whose first row is U's row t, so the
+    largest |entry| of every pivot row is the diagonal entry +-8, unique. The
+    pivot of step t is therefore U[t, t] in original column perm[t], and every
+    intermediate value is a small dyadic rational (exact in FP32 and in TF32 /
+    BF16 splits). det A = prod(diag U) * sgn(P).
+    """
+    rng = np.random.default_rng(seed)
+    L = np.eye(n)
+    mask = rng.random((n, n)) < density
+    vals = rng.choice([-1.0, 1.0], size=(n, n))
+    L += np.tril(mask * vals, -1)
+    U = np.triu(rng.choice([-1.0, 0.0, 1.0], size=(n, n)), 1)
+    d = rng.choice([-8.0, 8.0], size=n)
+    U[np.diag_indices(n)] = d
+    perm = rng.permutation(n)
+    M = L @ U
+    A = np.empty_like(M)
+    A[:, perm] = M  # column t of L U lands in original column perm[t]
+    inv = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            inv += perm[i] > perm[j]
+    det_sign = (-1.0 if inv % 2 else 1.0) * float(np.prod(np.sign(d)))
+    logabs = n * math.log(8.0)
+    return A, det_sign, logabs, perm.astype(np.int64)
