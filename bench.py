@@ -1,0 +1,306 @@
+"""Benchmark: condensation log-determinant throughput on GB300 (one JSON line).
+
+A step is one full condensation sweep (stage, every pivot step, finalize) of the
+N x N benchmark matrix through liblogdet. Throughput is counted as 2N^3/3 flop
+per sweep (TFLOP/s). Inputs: dense iid N(0, 1/N) entries, N = 8000, seed 1,
+generated with numpy's default_rng (bit-identical on every host).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f64_plain]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+With N > 1 (torchrun), every rank runs an independent replica of the sweep (a
+single matrix does not shard) and the value is the whole job's throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logdet TFLOP/s (2N³/3) and batched dets/s, mixed vs plain FP64 at stated error"
+UNIT = "TFLOP/s"
+N_DEFAULT = 8000
+SEED = 1
+
+# dominant kernel per mode: (profile class, bound, algorithmic bytes per element update)
+DOMINANT = {
+    "f64_plain": ("update", "hbm", 16),
+    "f32_plain": ("update", "hbm", 8),
+}
+DTYPE = {"f64_plain": "f64", "f32_plain": "f32", "f64_blocked": "f64", "f32_tf32": "f32+tf32",
+         "f32_3xtf32": "f32+3xtf32", "f32_bf16x3": "f32+bf16x3"}
+
+
+def flops(N):
+    return 2.0 * N ** 3 / 3.0
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.err = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", sel],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # no nvidia-smi: report why
+            self.err = str(e)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(A, target_s=12.0, threads=None):
+    """Times the oracle on the host cores over the first S pivot steps of A."""
+    import oracle
+
+    N = A.shape[0]
+    threads = threads or (os.cpu_count() or 1)
+    oracle.build()
+    s0 = min(N, 8)
+    t0 = time.perf_counter()
+    oracle.logdet(A, max_steps=s0, nthreads=threads)
+    t_cal = max(time.perf_counter() - t0, 1e-3)
+    S = int(max(s0, min(N, s0 * target_s / t_cal)))
+    t0 = time.perf_counter()
+    oracle.logdet(A, max_steps=S, nthreads=threads)
+    dt = time.perf_counter() - t0
+    fl = sum(2.0 * (N - s - 1) ** 2 for s in range(S))
+    return {"value": fl / dt / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {S} of {N} condensation steps of the N={N} benchmark matrix "
+                      f"({fl:.3g} flop in {dt:.2f} s, FP64, {threads} threads)"}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    import workloads
+    N = args.N
+    A = workloads.dense_gaussian(N, seed=SEED, var=1.0 / N)
+    # each step: a bounded sample of the sweep, sized so the whole run takes minutes
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(A, target_s=per_step * 0.3)
+    vals = []
+    samples = []
+    for _ in range(args.steps):
+        cb = oracle_sample(A, target_s=per_step)
+        vals.append(cb["value"])
+        samples.append(cb)
+    v = statistics.median(vals)
+    cb = dict(samples[-1])
+    cb["value"] = v
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": flops(N) / (v * 1e12) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"dense iid N(0,1/N) N={N} seed {SEED}, plain FP64 condensation "
+                               f"(oracle, host cores)", "N": N, "mode": "f64_plain"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, local, world = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1811_08057_gb300 as pk
+    from paper_1811_08057_gb300 import _lib
+    import workloads
+
+    N = args.N
+    mode = args.mode
+    A_np = workloads.dense_gaussian(N, seed=SEED, var=1.0 / N)
+    A = torch.from_numpy(A_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return pk.logdet(A, mode)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        sg, la = step()
+    barrier()
+
+    # accuracy of this result against the stored FP64 oracle value
+    err = None
+    gold = os.path.join(ROOT, "tests", "golden", f"oracle_dense_n{N}_seed{SEED}.json")
+    if os.path.exists(gold):
+        with open(gold) as f:
+            g = json.load(f)
+        err = {"logabs": float(la), "oracle_logabs": g["logabs"],
+               "rel_err": abs(float(la) - g["logabs"]) / max(1.0, abs(g["logabs"])),
+               "sign_match": float(sg) == g["sign"]}
+
+    kernel, bound, bytes_per_elem = DOMINANT.get(mode, ("update", "hbm", 8))
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    _lib.ld_profile_start(kernel)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sg, la = step()
+    e1.record(stream)
+    barrier()
+    _lib.ld_profile_stop()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches_all, _ = _lib.ld_profile_query(None)
+    k_launches, k_ms = _lib.ld_profile_query(kernel)
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    value = world * flops(N) / (ms_max * 1e-3) / 1e12
+
+    # roofline of the dominant kernel: algorithmic bytes over its event time
+    peaks = read_peaks()
+    alg_bytes = bytes_per_elem * (N - 1) * N * (2 * N - 1) / 6.0 * args.steps
+    achieved = alg_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
+    peak = peaks["hbm_gbs"]
+    roofline = {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": None, "peak_source": peaks["source"],
+                "kernel_ms_per_step": k_ms / args.steps,
+                "kernel_launches_per_step": k_launches / args.steps,
+                "algorithmic_bytes_per_step": alg_bytes / args.steps}
+
+    # end to end: pinned host input -> device -> sweep -> host result, per step
+    A_host = torch.from_numpy(A_np).pin_memory()
+    A_dev = torch.empty_like(A)
+    import ctypes
+    hs, hl = ctypes.c_double(), ctypes.c_double()
+    mcode = _lib.MODES[mode]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        code = _lib.ld_logdet(A_dev.data_ptr(), _lib.LD_DTYPE_F64, N, N, mcode,
+                              stream.cuda_stream, ctypes.addressof(hs), ctypes.addressof(hl))
+        _lib.check("ld_logdet", code)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * flops(N) / float(te[0]) / 1e12, "unit": UNIT,
+           "h2d_bytes_per_step": A_np.nbytes, "d2h_bytes_per_step": 16}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(A_np, target_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE.get(mode, mode), "data": "synthetic",
+            "config": {"workload": f"dense iid N(0,1/N) N={N} seed {SEED}, one sweep per step",
+                       "N": N, "mode": mode, "parallelism": "replicas" if world > 1 else "1 gpu",
+                       "l2": "inputs larger than L2 (N^2 elements > 129 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_all, "clocks": clk,
+            "accuracy": err,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="f64_plain")
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

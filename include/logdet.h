@@ -124,6 +124,21 @@ ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const i
                             const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,
                             void* stream, double* signs, double* logabs);
 
+/*
+ * Launch accounting for measurement (no counterpart in the paper). While on,
+ * every kernel launch is counted per kernel class ("stage", "pivot_factor",
+ * "update", "row_argmax", "finalize", ...) and launches of the class named by
+ * `kernel` (NULL or "" = all) are bracketed by CUDA events recorded on the
+ * launching stream. Process-global, not for concurrent use from several threads.
+ *   ld_profile_start  clears earlier results and switches accounting on
+ *   ld_profile_stop   switches it off, waits for the events and sums them
+ *   ld_profile_query  launches of class `kernel` (NULL = all) and their summed
+ *                     event time in milliseconds; LD_ERR_INVALID_ARG for NULL outs
+ */
+ld_status ld_profile_start(const char* kernel);
+ld_status ld_profile_stop(void);
+ld_status ld_profile_query(const char* kernel, int64_t* launches, double* total_ms);
+
 /* Human-readable name of a status code (static storage). */
 const char* ld_status_string(ld_status s);
 

@@ -1,0 +1,135 @@
+// C-ABI entry points of liblogdet (declared in include/logdet.h).
+#include <stdlib.h>
+#include <string.h>
+
+#include "record.cuh"
+
+namespace ld {
+
+// Stream-ordered scratch allocation. LD_FAULT_INJECT_ALLOC=1 in the environment
+// makes it fail, so the error path can be exercised without exhausting memory.
+ld_status scratch_alloc(void** p, size_t bytes, cudaStream_t stream) {
+  *p = nullptr;
+  const char* inj = getenv("LD_FAULT_INJECT_ALLOC");
+  if (inj && inj[0] == '1') return LD_ERR_ALLOC;
+  if (bytes == 0) bytes = kAlign;
+  cudaError_t e = cudaMallocAsync(p, bytes, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return LD_ERR_ALLOC;
+  }
+  return LD_OK;
+}
+
+void scratch_free(void* p, cudaStream_t stream) {
+  if (p) cudaFreeAsync(p, stream);
+}
+
+// True when ptr is device (or managed) memory that a kernel may write.
+bool is_device_pointer(const void* ptr) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static ld_status run_sweep(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
+                           bool keep, cudaStream_t stream) {
+  switch (r.mode) {
+    case LD_F64_PLAIN:
+      return run_plain<double>(A, a_dtype, lda, r, keep, stream);
+    case LD_F32_PLAIN:
+      return run_plain<float>(A, a_dtype, lda, r, keep, stream);
+    case LD_F64_BLOCKED:
+    case LD_F32_TF32:
+    case LD_F32_3XTF32:
+    case LD_F32_BF16X3:
+      return run_blocked(A, a_dtype, lda, r, keep, stream);
+  }
+  return LD_ERR_INVALID_ARG;
+}
+
+static ld_status logdet_impl(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda,
+                             ld_mode mode, void* stream_v, void* factors, double* sign,
+                             double* logabs) {
+  if (n < 0 || lda < (n > 0 ? n : 1) || (n > 0 && !A) || !sign || !logabs)
+    return LD_ERR_INVALID_ARG;
+  if (!mode_valid(mode) || (a_dtype != LD_DTYPE_F64 && a_dtype != LD_DTYPE_F32))
+    return LD_ERR_INVALID_ARG;
+  if (n > (int64_t)0x7fffffff) return LD_ERR_UNSUPPORTED;
+  if (factors && (reinterpret_cast<uintptr_t>(factors) % kAlign) != 0) return LD_ERR_INVALID_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  const size_t bytes = record_layout(n, mode, nullptr, nullptr);
+  void* base = factors;
+  void* owned = nullptr;
+  if (!base) {
+    ld_status as = scratch_alloc(&owned, bytes + kAlign, stream);
+    if (as != LD_OK) return as;
+    base = reinterpret_cast<void*>(align_up(reinterpret_cast<uintptr_t>(owned), kAlign));
+  }
+  Record r;
+  record_layout(n, mode, base, &r);
+  const bool sign_dev = is_device_pointer(sign);
+  const bool log_dev = is_device_pointer(logabs);
+  ld_status st = run_sweep(A, a_dtype, lda, r, factors != nullptr, stream);
+  if (st == LD_OK) st = launch_finalize(r, sign_dev ? sign : nullptr, log_dev ? logabs : nullptr, stream);
+  if (st == LD_OK && (!sign_dev || !log_dev)) {
+    double host[2];
+    cudaError_t e = cudaMemcpyAsync(host, &r.header->sign, sizeof(host), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      st = LD_ERR_CUDA;
+    } else {
+      if (!sign_dev) *sign = host[0];
+      if (!log_dev) *logabs = host[1];
+    }
+  }
+  if (owned) scratch_free(owned, stream);
+  return st;
+}
+
+}  // namespace ld
+
+extern "C" {
+
+ld_status ld_logdet(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
+                    void* stream, double* sign, double* logabs) {
+  return ld::logdet_impl(A, a_dtype, n, lda, mode, stream, nullptr, sign, logabs);
+}
+
+size_t ld_factors_size(int64_t n, ld_mode mode) {
+  if (n < 0 || !ld::mode_valid(mode)) return 0;
+  return ld::record_layout(n, mode, nullptr, nullptr);
+}
+
+ld_status ld_logdet_factor(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
+                           void* stream, void* factors, double* sign, double* logabs) {
+  if (!factors) return LD_ERR_INVALID_ARG;
+  return ld::logdet_impl(A, a_dtype, n, lda, mode, stream, factors, sign, logabs);
+}
+
+const char* ld_status_string(ld_status s) {
+  switch (s) {
+    case LD_OK:
+      return "LD_OK";
+    case LD_ERR_INVALID_ARG:
+      return "LD_ERR_INVALID_ARG: bad size, leading dimension, pointer or enum";
+    case LD_ERR_UNSUPPORTED:
+      return "LD_ERR_UNSUPPORTED: request not supported by this build";
+    case LD_ERR_ALLOC:
+      return "LD_ERR_ALLOC: device memory allocation failed";
+    case LD_ERR_CUDA:
+      return "LD_ERR_CUDA: a CUDA call or kernel launch failed";
+    case LD_ERR_TIMEOUT:
+      return "LD_ERR_TIMEOUT: a bounded device-side wait gave up";
+  }
+  return "unknown ld_status";
+}
+
+const char* ld_version(void) { return "liblogdet 0.1 sm_103a"; }
+
+}  // extern "C"

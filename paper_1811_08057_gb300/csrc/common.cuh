@@ -1,0 +1,153 @@
+// Shared device-side definitions of liblogdet (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "logdet.h"
+
+namespace ld {
+
+// Flags of a sweep (SweepState::flags).
+enum : int {
+  kFlagSingular = 1,  // a pivot row was all zero: det A = 0 in the arithmetic used
+  kFlagNaN = 2,       // a pivot row held a NaN
+  kFlagTimeout = 4,   // a bounded device wait gave up
+  kFlagBadSize = 8    // a batched matrix larger than the reserved bound
+};
+
+// Running sign and compensated log-sum of one sweep (lives in device memory).
+struct SweepState {
+  double sign;  // product of sgn(p) and the Laplace / exchange signs so far
+  double sum;   // Neumaier-compensated sum of log|p|: value ...
+  double comp;  // ... and compensation
+  int flags;
+  int steps;    // pivots taken
+};
+
+// Candidate of the pivot-column search over one tile of a pivot row (Sec. 2.2).
+// Ordering: larger |v| wins; equal |v| goes to the smaller original column
+// label. NaN is recorded separately (any NaN makes the result NaN).
+struct Cand {
+  double absv;  // |v|, -1 for "no candidate"
+  double v;     // signed value
+  int label;    // original column label (colperm)
+  int pos;      // position in the current (swapped) layout
+  int nan;      // 1 if the tile held a NaN
+  int pad;
+};
+
+__device__ __forceinline__ void cand_init(Cand& c) {
+  c.absv = -1.0;
+  c.v = 0.0;
+  c.label = 0x7fffffff;
+  c.pos = -1;
+  c.nan = 0;
+  c.pad = 0;
+}
+
+__device__ __forceinline__ bool cand_better(double absv, int label, const Cand& b) {
+  return absv > b.absv || (absv == b.absv && label < b.label);
+}
+
+__device__ __forceinline__ void cand_offer(Cand& c, double v, int label, int pos) {
+  double a = fabs(v);
+  if (a != a) {
+    c.nan = 1;
+    return;
+  }
+  if (cand_better(a, label, c)) {
+    c.absv = a;
+    c.v = v;
+    c.label = label;
+    c.pos = pos;
+  }
+}
+
+__device__ __forceinline__ void cand_merge(Cand& c, const Cand& o) {
+  c.nan |= o.nan;
+  if (o.pos >= 0 && cand_better(o.absv, o.label, c)) {
+    c.absv = o.absv;
+    c.v = o.v;
+    c.label = o.label;
+    c.pos = o.pos;
+  }
+}
+
+__device__ __forceinline__ void cand_warp_reduce(Cand& c) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Cand o;
+    o.absv = __shfl_xor_sync(0xffffffffu, c.absv, off);
+    o.v = __shfl_xor_sync(0xffffffffu, c.v, off);
+    o.label = __shfl_xor_sync(0xffffffffu, c.label, off);
+    o.pos = __shfl_xor_sync(0xffffffffu, c.pos, off);
+    o.nan = __shfl_xor_sync(0xffffffffu, c.nan, off);
+    cand_merge(c, o);
+  }
+}
+
+// Block-wide reduction; every thread gets the result. `scratch` holds
+// blockDim.x / 32 entries.
+__device__ __forceinline__ void cand_block_reduce(Cand& c, Cand* scratch) {
+  cand_warp_reduce(c);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = c;
+  __syncthreads();
+  if (warp == 0) {
+    Cand t;
+    if (lane < nwarps)
+      t = scratch[lane];
+    else
+      cand_init(t);
+    cand_warp_reduce(t);
+    if (lane == 0) scratch[0] = t;
+  }
+  __syncthreads();
+  c = scratch[0];
+  __syncthreads();
+}
+
+// Neumaier step on the state's compensated sum.
+__device__ __forceinline__ void state_add_log(SweepState* st, double x) {
+  double s = st->sum;
+  double t = s + x;
+  if (fabs(s) >= fabs(x))
+    st->comp += (s - t) + x;
+  else
+    st->comp += (x - t) + s;
+  st->sum = t;
+}
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+}  // namespace ld
+
+// Host-side launch check: turns a launch error into LD_ERR_CUDA.
+#define LD_CHECK_LAUNCH()                                   \
+  do {                                                      \
+    cudaError_t e_ = cudaGetLastError();                    \
+    if (e_ != cudaSuccess) return LD_ERR_CUDA;              \
+  } while (0)
+
+#define LD_CHECK_CUDA(call)                                 \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return LD_ERR_CUDA;              \
+  } while (0)

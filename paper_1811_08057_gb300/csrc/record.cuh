@@ -1,0 +1,119 @@
+// Factor record layout and the internal launch interface of liblogdet.
+#pragma once
+
+#include "common.cuh"
+
+namespace ld {
+
+constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
+constexpr int kCandCols = 512;      // narrowest column tile of a candidate (FP64: 256 x double2)
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline bool mode_valid(int mode) { return mode >= LD_F64_PLAIN && mode <= LD_F32_BF16X3; }
+inline bool mode_is_f64(ld_mode mode) { return mode == LD_F64_PLAIN || mode == LD_F64_BLOCKED; }
+inline bool mode_is_blocked(ld_mode mode) {
+  return mode == LD_F64_BLOCKED || mode == LD_F32_TF32 || mode == LD_F32_3XTF32 ||
+         mode == LD_F32_BF16X3;
+}
+inline int64_t leading_dim(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), 32); }
+
+// Header at offset 0 of a factor record (256 bytes reserved).
+struct RecordHeader {
+  int64_t n;
+  int64_t ldf;
+  int32_t mode;
+  int32_t flags;
+  double sign;
+  double logabs;
+};
+
+// Device pointers into one factor record.
+struct Record {
+  char* base = nullptr;
+  int64_t n = 0, ldf = 0;
+  ld_mode mode = LD_F64_PLAIN;
+  RecordHeader* header = nullptr;
+  void* F = nullptr;         // n x ldf, element type of the mode
+  int* colperm = nullptr;    // n
+  int* pivpos = nullptr;     // n
+  double* pivval = nullptr;  // n
+  SweepState* state = nullptr;
+  Cand* cand = nullptr;      // ncand entries
+  int64_t ncand = 0;
+};
+
+// Computes the layout (and, if base != nullptr, the pointers). Returns the size.
+inline size_t record_layout(int64_t n, ld_mode mode, void* base, Record* r) {
+  const int64_t ldf = leading_dim(n);
+  const size_t es = mode_is_f64(mode) ? 8 : 4;
+  const int64_t ncand = ceil_div(n > 0 ? n : 1, kCandCols) + 1;
+  size_t off = 0;
+  const size_t o_hdr = off;
+  off += kAlign;
+  const size_t o_F = off;
+  off += align_up((size_t)n * (size_t)ldf * es, kAlign);
+  const size_t o_cp = off;
+  off += align_up((size_t)n * 4, kAlign);
+  const size_t o_pp = off;
+  off += align_up((size_t)n * 4, kAlign);
+  const size_t o_pv = off;
+  off += align_up((size_t)n * 8, kAlign);
+  const size_t o_st = off;
+  off += align_up(sizeof(SweepState), kAlign);
+  const size_t o_cd = off;
+  off += align_up((size_t)ncand * sizeof(Cand), kAlign);
+  if (r) {
+    char* b = static_cast<char*>(base);
+    r->base = b;
+    r->n = n;
+    r->ldf = ldf;
+    r->mode = mode;
+    r->header = reinterpret_cast<RecordHeader*>(b + o_hdr);
+    r->F = b + o_F;
+    r->colperm = reinterpret_cast<int*>(b + o_cp);
+    r->pivpos = reinterpret_cast<int*>(b + o_pp);
+    r->pivval = reinterpret_cast<double*>(b + o_pv);
+    r->state = reinterpret_cast<SweepState*>(b + o_st);
+    r->cand = reinterpret_cast<Cand*>(b + o_cd);
+    r->ncand = ncand;
+  }
+  return off;
+}
+
+int device_sm_count();
+
+// ---- plain-path launchers (plain.cu) ----
+// Copies A into F (converting to the storage type), sets colperm = identity,
+// resets the sweep state and writes the pivot candidates of row 0.
+template <typename T>
+ld_status launch_stage(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
+                       cudaStream_t stream);
+// Pivot choice (from the candidates of row s), row factoring (Eq. (3), Sec. 2.3),
+// column exchange to the boundary (Sec. 2.4) for rows >= swap_row_begin, sign
+// and log-sum update.
+template <typename T>
+ld_status launch_pivot_factor(const Record& r, int64_t s, int64_t swap_row_begin,
+                              cudaStream_t stream);
+// Rank-1 update (Eq. (2) with a unit pivot) of rows s+1 .. row_end-1, with the
+// pivot-column search of row s+1 fused in when lookahead is set.
+template <typename T>
+ld_status launch_update(const Record& r, int64_t s, int64_t row_end, bool lookahead,
+                        cudaStream_t stream);
+// Pivot candidates of row `row` over the active columns [0, m).
+template <typename T>
+ld_status launch_row_argmax(const Record& r, int64_t row, int64_t m, cudaStream_t stream);
+// Writes sign / logabs into the header and, if given, into device outputs.
+ld_status launch_finalize(const Record& r, double* d_sign, double* d_logabs, cudaStream_t stream);
+// Whole plain sweep (stage, n pivot steps, finalize).
+template <typename T>
+ld_status run_plain(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
+                    bool keep_factors, cudaStream_t stream);
+
+// ---- blocked path (blocked.cu) ----
+ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
+                      bool keep_factors, cudaStream_t stream);
+
+}  // namespace ld
