@@ -17,8 +17,10 @@
  * Conventions (all entry points):
  *   - Matrices are row-major with a leading dimension (elements between row
  *     starts) lda >= n. Inputs are never modified.
- *   - Every function returns an ld_status; nothing traps or aborts. Device-side
- *     errors are reported through the status of the call that observes them.
+ *   - Every function returns an ld_status; nothing traps or aborts. A bounded
+ *     device-side wait that gives up sets a flag in the sweep: the results become
+ *     NaN, the factor record header's flags field has bit 4 set, and a call that
+ *     reads its results back to the host returns LD_ERR_TIMEOUT.
  *   - n == 0 gives sign 1, logabs 0. An all-zero pivot row gives sign 0 and
  *     logabs -inf with LD_OK (the matrix is singular in the arithmetic used).
  *     A NaN in any pivot row gives NaN for both.
@@ -138,6 +140,25 @@ ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const i
 ld_status ld_profile_start(const char* kernel);
 ld_status ld_profile_stop(void);
 ld_status ld_profile_query(const char* kernel, int64_t* launches, double* total_ms);
+
+/*
+ * ld_rankb_update - the trailing update of the blocked sweep on its own:
+ *   D[M x N] -= A[M x K] * B[N x K]^T
+ * (block condensation, the paper's future-work extension of Eq. (2)).
+ *   mode   LD_F64_BLOCKED: FP64 A, B, D, FP64 FMAs on the CUDA cores;
+ *          LD_F32_TF32 / LD_F32_3XTF32 / LD_F32_BF16X3: FP32 A, B, D, products on
+ *          the tensor cores (tcgen05, TMA-fed) with FP32 accumulation, operands
+ *          used as TF32, split hi+lo at TF32, or split hi+lo at BF16
+ *          (hi*hi + hi*lo + lo*hi)
+ *   A, B, D  device, row-major, leading dimensions lda >= K, ldb >= K, ldd >= N;
+ *          for the tensor-core modes K must be a multiple of 64, D 16-byte
+ *          aligned and ldd a multiple of 4 (else LD_ERR_UNSUPPORTED)
+ * Allocates stream-ordered scratch and waits for `stream` before returning (to
+ * report LD_ERR_TIMEOUT from a device wait).
+ */
+ld_status ld_rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A,
+                          int64_t lda, const void* B, int64_t ldb, void* D, int64_t ldd,
+                          void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* ld_status_string(ld_status s);

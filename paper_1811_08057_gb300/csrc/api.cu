@@ -78,14 +78,15 @@ static ld_status logdet_impl(const void* A, ld_dtype a_dtype, int64_t n, int64_t
   ld_status st = run_sweep(A, a_dtype, lda, r, factors != nullptr, stream);
   if (st == LD_OK) st = launch_finalize(r, sign_dev ? sign : nullptr, log_dev ? logabs : nullptr, stream);
   if (st == LD_OK && (!sign_dev || !log_dev)) {
-    double host[2];
-    cudaError_t e = cudaMemcpyAsync(host, &r.header->sign, sizeof(host), cudaMemcpyDeviceToHost, stream);
+    RecordHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, r.header, sizeof(h), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
       st = LD_ERR_CUDA;
     } else {
-      if (!sign_dev) *sign = host[0];
-      if (!log_dev) *logabs = host[1];
+      if (!sign_dev) *sign = h.sign;
+      if (!log_dev) *logabs = h.logabs;
+      if (h.flags & kFlagTimeout) st = LD_ERR_TIMEOUT;
     }
   }
   if (owned) scratch_free(owned, stream);

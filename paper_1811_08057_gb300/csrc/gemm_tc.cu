@@ -1,0 +1,415 @@
+// Trailing rank-b update of the blocked sweep on the 5th-generation tensor cores:
+//   D[M x N] -= A[M x K] * B[N x K]^T      (FP32 accumulate in TMEM)
+// A holds the multipliers of the b panel pivots for each trailing row, B the
+// factored panel rows (transposed), D the trailing block. Precision modes:
+//   TF32    one kind::tf32 MMA per K-step on the FP32 operands,
+//   3xTF32  A = Ah + Al, B = Bh + Bl split at TF32 precision; Al*Bh + Ah*Bl + Ah*Bh,
+//   BF16x3  the same split at BF16 precision with kind::f16 MMAs.
+// Per CTA: one 128 x BN output tile; warp 0 lane 0 issues TMA loads of 128-byte
+// K-chunks into a ring of shared-memory stages, warp 1 lane 0 issues tcgen05.mma
+// into a TMEM accumulator and frees stages with tcgen05.commit, then all four
+// warps read the accumulator (tcgen05.ld) and apply D -= acc.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "profile.cuh"
+#include "record.cuh"
+#include "tc.cuh"
+
+namespace ld {
+
+enum TcKind { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
+
+namespace {
+
+template <int KIND>
+struct TcCfg {
+  static constexpr int BM = 128;
+  static constexpr int BN = 128;
+  static constexpr int ES = (KIND == kBF16x3) ? 2 : 4;
+  static constexpr int BK = 128 / ES;  // elements in one 128-byte K-chunk
+  static constexpr int NT = (KIND == kTF32) ? 1 : 2;
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = (KIND == kTF32) ? 4 : 3;
+  static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
+  static constexpr int NSUB = BK / KSTEP;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                    float* __restrict__ D, int64_t ldd, int M, int N, int K, int* __restrict__ err) {
+  using C = TcCfg<KIND>;
+  constexpr uint32_t IDESC = tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, C::BM, C::BN);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * C::BN;
+  const int nk = K / C::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accf, 1);
+    tc::fence_mbar_init();
+    tc::tma_prefetch_desc(&mAh);
+    tc::tma_prefetch_desc(&mBh);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, C::BN);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    // producer: one K-chunk of every operand tile per stage
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % C::STAGES, r = kc / C::STAGES;
+      if (!tc::mbar_wait(&empty[s], (r & 1) ^ 1, err)) break;
+      uint8_t* st = smem + s * C::STAGE_BYTES;
+      tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+      tc::tma_load_2d(st, &mAh, &full[s], kc * C::BK, m0);
+      tc::tma_load_2d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0);
+      if (C::NT == 2) {
+        tc::tma_load_2d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0);
+        tc::tma_load_2d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0);
+      }
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    uint32_t acc = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % C::STAGES, r = kc / C::STAGES;
+      if (!tc::mbar_wait(&full[s], r & 1, err)) break;
+      tc::tc_fence_after();
+      const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
+      const uint32_t ah = st, al = st + C::A_BYTES;
+      const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
+#pragma unroll
+      for (int k = 0; k < C::NSUB; ++k) {
+        const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
+        if (KIND == kTF32) {
+          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+        } else if (KIND == kTF32x3) {
+          tc::mma_tf32(tmem, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+        } else {
+          tc::mma_f16(tmem, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_f16(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_f16(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+        }
+        acc = 1u;
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(accf);
+  }
+  __syncwarp();
+
+  // epilogue: D -= acc, one TMEM lane (= one output row) per thread
+  const bool got = tc::mbar_wait(accf, 0, err);
+  __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
+  tc::tc_fence_after();
+  const bool clean = got && (*reinterpret_cast<volatile int*>(err) == 0);
+  const int row = m0 + warp * 32 + lane;
+  float* drow = D + (int64_t)row * ldd;
+#pragma unroll 1
+  for (int c = 0; c < C::BN / 32; ++c) {
+    float a[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), a);
+    const int col0 = n0 + c * 32;
+    if (clean && row < M) {
+      if (col0 + 32 <= N) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float4 v = *reinterpret_cast<float4*>(drow + col0 + 4 * q);
+          v.x -= a[4 * q + 0];
+          v.y -= a[4 * q + 1];
+          v.z -= a[4 * q + 2];
+          v.w -= a[4 * q + 3];
+          *reinterpret_cast<float4*>(drow + col0 + 4 * q) = v;
+        }
+      } else {
+        for (int q = 0; q < 32 && col0 + q < N; ++q) drow[col0 + q] -= a[q];
+      }
+    }
+  }
+
+  // teardown: every issued TMA copy has landed before shared memory is released
+  // (only the last round of each stage: an mbarrier reports the parity of its
+  // current phase, so an older round of the same parity would look pending)
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < C::STAGES && s < issued; ++s) {
+      const int last = (issued - 1 - s) / C::STAGES;
+      tc::mbar_wait(&full[s], last & 1, err);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, C::BN);
+}
+
+// --------------------------------------------------- operand preparation
+// Splits rows x K (leading dimension ldx) FP32 values into compact hi / lo
+// buffers (rows x K). TF32: hi keeps the sign, exponent and top 10 mantissa bits,
+// lo = x - hi (exact). BF16: hi = bf16(x), lo = bf16(x - hi). Plain TF32 copies.
+template <int KIND, typename Out>
+__global__ void split_kernel(const float* __restrict__ X, int64_t ldx, int rows, int K,
+                            Out* __restrict__ hi, Out* __restrict__ lo) {
+  const int64_t total = (int64_t)rows * K;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / K, k = idx % K;
+    const float x = X[i * ldx + k];
+    if constexpr (KIND == kBF16x3) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      hi[idx] = h;
+      lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+    } else if constexpr (KIND == kTF32x3) {
+      const float h = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+      hi[idx] = h;
+      lo[idx] = x - h;
+    } else {
+      hi[idx] = x;
+    }
+  }
+}
+
+// --------------------------------------------------- FP64 SIMT rank-b update
+// D -= A * B^T in FP64 on the CUDA cores (64 x 64 tiles, 4 x 4 per thread).
+__global__ void __launch_bounds__(256)
+    rankb_f64_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+                     int64_t ldb, double* __restrict__ D, int64_t ldd, int M, int N, int K) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e % 16, rr = e / 16;
+      const int ar = m0 + rr, br = n0 + rr;
+      As[kk][rr] = (ar < M && k0 + kk < K) ? A[(int64_t)ar * lda + k0 + kk] : 0.0;
+      Bs[kk][rr] = (br < N && k0 + kk < K) ? B[(int64_t)br * ldb + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (c < N) D[(int64_t)r * ldd + c] -= acc[i][j];
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// K-major operand (rows x K, compact) as a TMA map with 128-byte swizzled
+// boxes of box_rows rows.
+bool make_map(CUtensorMap* map, const void* base, int rows, int K, int es, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((size_t)K * es) % 16 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND>
+ld_status launch_tc(const void* ah, const void* al, const void* bh, const void* bl, int M, int N,
+                    int K, float* D, int64_t ldd, int* err, cudaStream_t stream) {
+  using C = TcCfg<KIND>;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, ah, M, K, C::ES, C::BM) || !make_map(&mBh, bh, N, K, C::ES, C::BN))
+    return LD_ERR_CUDA;
+  if (C::NT == 2) {
+    if (!make_map(&mAl, al, M, K, C::ES, C::BM) || !make_map(&mBl, bl, N, K, C::ES, C::BN))
+      return LD_ERR_CUDA;
+  } else {
+    mAl = mAh;
+    mBl = mBh;
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(rankb_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::SMEM) != cudaSuccess)
+      return LD_ERR_CUDA;
+    attr_set = true;
+  }
+  dim3 grid((unsigned)ceil_div(N, C::BN), (unsigned)ceil_div(M, C::BM));
+  ProfScope ps("rankb_tc", stream);
+  rankb_tc_kernel<KIND><<<grid, 128, C::SMEM, stream>>>(mAh, mAl, mBh, mBl, D, ldd, M, N, K, err);
+  LD_CHECK_LAUNCH();
+  return LD_OK;
+}
+
+}  // namespace
+
+// Bytes of scratch needed by rankb_update for an M x N x K update in `mode`.
+size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K) {
+  if (mode == LD_F64_BLOCKED) return kAlign;
+  const size_t es = (mode == LD_F32_BF16X3) ? 2 : 4;
+  const size_t parts = (mode == LD_F32_TF32) ? 1 : 2;
+  return align_up((size_t)M * K * es, kAlign) * parts + align_up((size_t)N * K * es, kAlign) * parts +
+         kAlign;
+}
+
+// D -= A * B^T with A (M x K, lda), B (N x K, ldb); FP64 for LD_F64_BLOCKED,
+// FP32 storage + tensor cores for the TF32 / 3xTF32 / BF16x3 modes. scratch holds
+// rankb_scratch_bytes(...) bytes (256-B aligned); err is a device int.
+ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
+                       cudaStream_t stream) {
+  if (M <= 0 || N <= 0 || K <= 0) return LD_OK;
+  if (mode == LD_F64_BLOCKED) {
+    dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
+    ProfScope ps("rankb_f64", stream);
+    rankb_f64_kernel<<<grid, 256, 0, stream>>>(static_cast<const double*>(A), lda,
+                                               static_cast<const double*>(B), ldb,
+                                               static_cast<double*>(D), ldd, (int)M, (int)N, (int)K);
+    LD_CHECK_LAUNCH();
+    return LD_OK;
+  }
+  if (K % 64 != 0) return LD_ERR_UNSUPPORTED;
+  const size_t es = (mode == LD_F32_BF16X3) ? 2 : 4;
+  const bool two = mode != LD_F32_TF32;
+  char* p = static_cast<char*>(scratch);
+  char* ah = p;
+  p += align_up((size_t)M * K * es, kAlign);
+  char* al = two ? p : nullptr;
+  if (two) p += align_up((size_t)M * K * es, kAlign);
+  char* bh = p;
+  p += align_up((size_t)N * K * es, kAlign);
+  char* bl = two ? p : nullptr;
+  const int sm = device_sm_count();
+  const int gA = (int)std::min<int64_t>(sm * 4, ceil_div(M * K, 256));
+  const int gB = (int)std::min<int64_t>(sm * 4, ceil_div(N * K, 256));
+  {
+    ProfScope ps("split", stream);
+    if (mode == LD_F32_BF16X3) {
+      split_kernel<kBF16x3, __nv_bfloat16><<<gA, 256, 0, stream>>>(
+          static_cast<const float*>(A), lda, (int)M, (int)K, reinterpret_cast<__nv_bfloat16*>(ah),
+          reinterpret_cast<__nv_bfloat16*>(al));
+      split_kernel<kBF16x3, __nv_bfloat16><<<gB, 256, 0, stream>>>(
+          static_cast<const float*>(B), ldb, (int)N, (int)K, reinterpret_cast<__nv_bfloat16*>(bh),
+          reinterpret_cast<__nv_bfloat16*>(bl));
+    } else if (mode == LD_F32_3XTF32) {
+      split_kernel<kTF32x3, float><<<gA, 256, 0, stream>>>(static_cast<const float*>(A), lda,
+                                                           (int)M, (int)K, reinterpret_cast<float*>(ah),
+                                                           reinterpret_cast<float*>(al));
+      split_kernel<kTF32x3, float><<<gB, 256, 0, stream>>>(static_cast<const float*>(B), ldb,
+                                                           (int)N, (int)K, reinterpret_cast<float*>(bh),
+                                                           reinterpret_cast<float*>(bl));
+    } else {
+      split_kernel<kTF32, float><<<gA, 256, 0, stream>>>(static_cast<const float*>(A), lda, (int)M,
+                                                         (int)K, reinterpret_cast<float*>(ah), nullptr);
+      split_kernel<kTF32, float><<<gB, 256, 0, stream>>>(static_cast<const float*>(B), ldb, (int)N,
+                                                         (int)K, reinterpret_cast<float*>(bh), nullptr);
+    }
+  }
+  LD_CHECK_LAUNCH();
+  float* Df = static_cast<float*>(D);
+  if ((ldd % 4) != 0 || (reinterpret_cast<uintptr_t>(D) & 15) != 0) return LD_ERR_UNSUPPORTED;
+  switch (mode) {
+    case LD_F32_TF32:
+      return launch_tc<kTF32>(ah, nullptr, bh, nullptr, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+    case LD_F32_3XTF32:
+      return launch_tc<kTF32x3>(ah, al, bh, bl, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+    case LD_F32_BF16X3:
+      return launch_tc<kBF16x3>(ah, al, bh, bl, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+    default:
+      return LD_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace ld
+
+extern "C" ld_status ld_rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A,
+                                     int64_t lda, const void* B, int64_t ldb, void* D, int64_t ldd,
+                                     void* stream_v) {
+  using namespace ld;
+  if (!mode_is_blocked(mode)) return LD_ERR_INVALID_ARG;
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldd < N) return LD_ERR_INVALID_ARG;
+  if (M == 0 || N == 0 || K == 0) return LD_OK;
+  if (!A || !B || !D) return LD_ERR_INVALID_ARG;
+  if (mode != LD_F64_BLOCKED && K % 64 != 0) return LD_ERR_UNSUPPORTED;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  void* scratch = nullptr;
+  ld_status st = scratch_alloc(&scratch, rankb_scratch_bytes(mode, M, N, K) + 2 * kAlign, stream);
+  if (st != LD_OK) return st;
+  char* base = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
+  int* err = reinterpret_cast<int*>(base);
+  if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) st = LD_ERR_CUDA;
+  if (st == LD_OK)
+    st = rankb_update(mode, M, N, K, A, lda, B, ldb, D, ldd, base + kAlign, err, stream);
+  int herr = 0;
+  if (st == LD_OK) {
+    if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      st = LD_ERR_CUDA;
+    else if (herr & kFlagTimeout)
+      st = LD_ERR_TIMEOUT;
+  }
+  scratch_free(scratch, stream);
+  return st;
+}

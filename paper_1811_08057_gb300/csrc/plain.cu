@@ -242,7 +242,7 @@ __global__ void finalize_kernel(const SweepState* __restrict__ st, RecordHeader*
   if (h->n == 0) {
     sg = 1.0;
     la = 0.0;
-  } else if (flags & kFlagNaN) {
+  } else if (flags & (kFlagNaN | kFlagTimeout | kFlagBadSize)) {
     sg = __longlong_as_double(0x7ff8000000000000ULL);
     la = sg;
   } else if (flags & kFlagSingular) {

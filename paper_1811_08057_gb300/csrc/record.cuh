@@ -112,6 +112,16 @@ template <typename T>
 ld_status run_plain(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                     bool keep_factors, cudaStream_t stream);
 
+// ---- scratch (api.cu) ----
+ld_status scratch_alloc(void** p, size_t bytes, cudaStream_t stream);
+void scratch_free(void* p, cudaStream_t stream);
+
+// ---- tensor-core / FP64 rank-b update (gemm_tc.cu) ----
+size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K);
+ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
+                       cudaStream_t stream);
+
 // ---- blocked path (blocked.cu) ----
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                       bool keep_factors, cudaStream_t stream);

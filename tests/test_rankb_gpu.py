@@ -1,0 +1,68 @@
+"""The trailing rank-b update D -= A B^T through the C ABI (ld_rankb_update).
+
+Compared element by element with the same update in FP64 on the host. Bounds,
+relative to |D| + |A| |B|^T per element (u = unit roundoff of the input format):
+  TF32   inputs carry 10 explicit mantissa bits: a few 2^-10, bound 4e-3;
+  3xTF32 the dropped lo*lo term and FP32 accumulation: ~2^-20, bound 5e-6;
+  BF16x3 hi and lo carry 8 bits each, lo*lo dropped: ~2^-16, bound 1e-4;
+  FP64   K FMAs in FP64: bound 1e-14.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1811_08057_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"f64_blocked": (1, torch.float64, 1e-14), "f32_tf32": (3, torch.float32, 4e-3),
+         "f32_3xtf32": (4, torch.float32, 5e-6), "f32_bf16x3": (5, torch.float32, 1e-4)}
+
+SHAPES = [(128, 128, 64), (1, 1, 64), (129, 257, 128), (300, 1000, 128), (1000, 300, 256),
+          (37, 5, 64), (2048, 2048, 128)]
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+@pytest.mark.parametrize("shape", SHAPES)
+def test_rankb_update_matches_fp64(mode, shape):
+    code, dt, tol = MODES[mode]
+    M, N, K = shape
+    g = torch.Generator().manual_seed(M * 7919 + N * 31 + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).to(dt)
+    B = torch.randn(N, K, generator=g, dtype=torch.float64).to(dt)
+    D = torch.randn(M, N, generator=g, dtype=torch.float64).to(dt)
+    want = D.double() - A.double() @ B.double().T
+    scale = D.double().abs() + A.double().abs() @ B.double().abs().T
+    Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()
+    rc = _lib.ld_rankb_update(code, M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K, Dd.data_ptr(), N,
+                              torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, _lib.STATUS.get(rc)
+    got = Dd.double().cpu()
+    err = ((got - want).abs() / scale).max().item()
+    assert err <= tol, f"{mode} {shape}: {err:.3e} > {tol:.1e}"
+
+
+def test_rankb_strided_leading_dims():
+    """Leading dimensions larger than the logical widths (views into bigger buffers)."""
+    M, N, K = 200, 150, 64
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(M, K + 64, generator=g)
+    B = torch.randn(N, K + 128, generator=g)
+    D = torch.randn(M, N + 12, generator=g)
+    want = D[:, :N].double() - A[:, :K].double() @ B[:, :K].double().T
+    Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()
+    rc = _lib.ld_rankb_update(4, M, N, K, Ad.data_ptr(), K + 64, Bd.data_ptr(), K + 128,
+                              Dd.data_ptr(), N + 12, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    got = Dd.cpu()
+    assert torch.equal(got[:, N:], D[:, N:]), "columns beyond N were touched"
+    scale = D[:, :N].double().abs() + A[:, :K].double().abs() @ B[:, :K].double().abs().T
+    assert ((got[:, :N].double() - want).abs() / scale).max().item() <= 5e-6
+
+
+def test_rankb_rejects_bad_k():
+    A = torch.zeros(8, 40, device="cuda")
+    assert _lib.ld_rankb_update(4, 8, 8, 40, A.data_ptr(), 40, A.data_ptr(), 40, A.data_ptr(), 40,
+                                None) == 2
+    assert _lib.ld_rankb_update(0, 8, 8, 64, A.data_ptr(), 64, A.data_ptr(), 64, A.data_ptr(), 64,
+                                None) == 1
