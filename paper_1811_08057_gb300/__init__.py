@@ -24,4 +24,11 @@ from ._lib import (  # noqa: F401
     ld_version,
     load,
 )
-from .api import Factors, logdet, logdet_factor, parse_factors  # noqa: F401
+from .api import (  # noqa: F401
+    BatchedInputs,
+    Factors,
+    logdet,
+    logdet_batched,
+    logdet_factor,
+    parse_factors,
+)

@@ -111,3 +111,47 @@ def logdet_factor(A: torch.Tensor, mode="f64_plain", stream=None) -> Factors:
                                  out.data_ptr() + 8)
     _lib.check("ld_logdet_factor", code)
     return parse_factors(record, n, mode)
+
+
+class BatchedInputs:
+    """Device arrays (pointers, sizes, leading dimensions) for ld_logdet_batched.
+
+    Keeps references to the matrices so their memory outlives the arrays. Build it
+    once and reuse it across calls (or CUDA-graph replays).
+    """
+
+    def __init__(self, mats, device=None):
+        if len(mats) == 0:
+            raise ValueError("empty batch")
+        dt = mats[0].dtype
+        for A in mats:
+            _check_matrix(A)
+            if A.dtype != dt:
+                raise TypeError("all matrices must share one dtype")
+        device = device or mats[0].device
+        self.mats = list(mats)
+        self.dtype_code = _dtype_code(mats[0])
+        self.count = len(mats)
+        self.n_max = max(A.shape[0] for A in mats)
+        self.ptrs = torch.tensor([A.data_ptr() for A in mats], dtype=torch.int64, device=device)
+        self.n = torch.tensor([A.shape[0] for A in mats], dtype=torch.int64, device=device)
+        self.lda = torch.tensor([max(A.stride(0), 1) if A.shape[0] else 1 for A in mats],
+                                dtype=torch.int64, device=device)
+
+
+def logdet_batched(batch, mode="f32_plain", stream=None, out=None):
+    """sign and log|det| of every matrix of a batch (list of CUDA tensors or a
+    BatchedInputs) in one persistent launch. Returns (signs, logabs) FP64 tensors."""
+    if not isinstance(batch, BatchedInputs):
+        batch = BatchedInputs(batch)
+    if out is None:
+        signs = torch.empty(batch.count, dtype=torch.float64, device=batch.ptrs.device)
+        logabs = torch.empty(batch.count, dtype=torch.float64, device=batch.ptrs.device)
+    else:
+        signs, logabs = out
+    code = _lib.ld_logdet_batched(batch.ptrs.data_ptr(), batch.dtype_code, batch.n.data_ptr(),
+                                  batch.lda.data_ptr(), batch.count, batch.n_max,
+                                  _mode_code(mode), _stream_handle(stream), signs.data_ptr(),
+                                  logabs.data_ptr())
+    _lib.check("ld_logdet_batched", code)
+    return signs, logabs

@@ -1,10 +1,346 @@
-// Batched condensation sweeps of many independent matrices.
+// Batched condensation sweeps: many independent matrices (e.g. the covariance
+// matrices of a Gaussian mixture, Sec. 1) in one persistent launch.
+//
+// Each CTA takes matrices from a queue ordered by decreasing size (longest
+// processing time first) and runs the whole sweep of one matrix by itself:
+//   - the matrix is copied into a per-CTA workspace (global memory, L2-resident);
+//   - panels of KB pivot rows live in shared memory; for each pivot row: max-abs
+//     column search (Sec. 2.2), exchange of the pivot column with the boundary
+//     column (Sec. 2.4), row factoring with an IEEE divide (Eq. (3)), rank-1
+//     update of the remaining panel rows (Eq. (2));
+//   - the rows below the panel then receive the panel's column exchanges and all
+//     KB rank-1 updates at once: their multipliers by forward substitution, then
+//     a <- fma(-c_t, r_t, a) for t = 0..KB-1 in pivot order, with a held in a
+//     register. Every element therefore sees exactly the plain sweep's sequence
+//     of operations (bit-identical results), while the trailing rows are read and
+//     written once per panel instead of once per pivot.
+#include <algorithm>
+
+#include "profile.cuh"
 #include "record.cuh"
+
+namespace ld {
+
+namespace {
+
+constexpr int kBT = 256;  // threads per CTA
+constexpr int kKB = 16;   // pivots per panel
+
+struct BatchedArgs {
+  const void* const* A_ptrs;
+  const int64_t* n;
+  const int64_t* lda;
+  int a_dtype;
+  int count;
+  int n_max;
+  int64_t ldw;
+  const int* order;
+  int* counter;
+  double* signs;
+  double* logabs;
+};
+
+// Counting sort of the matrix indices by decreasing size (one CTA).
+__global__ void order_kernel(const int64_t* __restrict__ n, int count, int n_max,
+                             int* __restrict__ order, int* __restrict__ counter,
+                             int* __restrict__ hist) {
+  for (int v = threadIdx.x; v <= n_max + 1; v += blockDim.x) hist[v] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int64_t v = n[i];
+    const int key = (v < 0 || v > n_max) ? n_max + 1 : (int)v;  // invalid sizes first
+    atomicAdd(&hist[key], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int v = n_max + 1; v >= 0; --v) {
+      const int c = hist[v];
+      hist[v] = run;
+      run += c;
+    }
+    *counter = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    int64_t v = n[i];
+    const int key = (v < 0 || v > n_max) ? n_max + 1 : (int)v;
+    order[atomicAdd(&hist[key], 1)] = i;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T load_in(const void* A, int a_dtype, int64_t idx) {
+  return a_dtype == LD_DTYPE_F64 ? static_cast<T>(static_cast<const double*>(A)[idx])
+                                 : static_cast<T>(static_cast<const float*>(A)[idx]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBT)
+    batched_kernel(BatchedArgs args, T* __restrict__ ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_max = args.n_max;
+  const int pw = n_max + 1;                                   // panel row pitch
+  T* P = reinterpret_cast<T*>(smem_raw);                      // kKB x pw
+  int* label = reinterpret_cast<int*>(P + kKB * pw);          // n_max
+  int* moved_dst = label + n_max;                             // 2 kKB
+  int* moved_src = moved_dst + 2 * kKB;                       // 2 kKB
+  __shared__ Cand red[kBT / 32];
+  __shared__ int s_mat, s_l, s_bad, s_nmoved;
+  __shared__ double s_p;
+  __shared__ int s_swap[kKB];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* W = ws + (int64_t)blockIdx.x * n_max * args.ldw;
+  const int64_t ldw = args.ldw;
+
+  while (true) {
+    if (tid == 0) {
+      const int q = atomicAdd(args.counter, 1);
+      s_mat = (q < args.count) ? args.order[q] : -1;
+    }
+    __syncthreads();
+    const int mat = s_mat;
+    if (mat < 0) break;
+    const int64_t n64 = args.n[mat];
+    if (n64 <= 0 || n64 > n_max) {
+      if (tid == 0) {
+        const bool empty = (n64 == 0);
+        args.signs[mat] = empty ? 1.0 : __longlong_as_double(0x7ff8000000000000ULL);
+        args.logabs[mat] = empty ? 0.0 : __longlong_as_double(0x7ff8000000000000ULL);
+      }
+      __syncthreads();
+      continue;
+    }
+    const int n = (int)n64;
+    const int64_t lda = args.lda[mat];
+    const void* A = args.A_ptrs[mat];
+    // stage the matrix into the CTA's workspace (a0)
+    for (int64_t e = tid; e < (int64_t)n * n; e += kBT) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      W[(int64_t)i * ldw + j] = load_in<T>(A, args.a_dtype, (int64_t)i * lda + j);
+    }
+    for (int j = tid; j < n; j += kBT) label[j] = j;
+    double sign = 1.0, sum = 0.0, comp = 0.0;  // meaningful in thread 0
+    int flags = 0;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+
+    for (int s0 = 0; s0 < n; s0 += kKB) {
+      const int bb = min(kKB, n - s0);
+      const int m0 = n - s0;
+      // panel rows into shared memory
+      for (int e = tid; e < bb * m0; e += kBT) {
+        const int t = e / m0, j = e % m0;
+        P[t * pw + j] = W[(int64_t)(s0 + t) * ldw + j];
+      }
+      __syncthreads();
+      for (int t = 0; t < bb; ++t) {
+        const int m = m0 - t;
+        // pivot column of panel row t (Sec. 2.2), ties to the smallest label
+        Cand c;
+        cand_init(c);
+        for (int j = tid; j < m; j += kBT) cand_offer(c, (double)P[t * pw + j], label[j], j);
+        cand_block_reduce(c, red);
+        if (tid == 0) {
+          if (c.nan || c.pos < 0 || c.absv == 0.0) {
+            s_bad = c.nan ? kFlagNaN : kFlagSingular;
+          } else {
+            const int l = c.pos;
+            double sg = sign;
+            if (c.v < 0.0) sg = -sg;
+            if (((m + 1) & 1) != 0) sg = -sg;
+            if (l != m - 1) sg = -sg;
+            sign = sg;
+            const double x = log(fabs(c.v));
+            const double tt = sum + x;
+            if (fabs(sum) >= fabs(x))
+              comp += (sum - tt) + x;
+            else
+              comp += (x - tt) + sum;
+            sum = tt;
+            const int lab = label[l];
+            label[l] = label[m - 1];
+            label[m - 1] = lab;
+            s_swap[t] = l;
+            s_l = l;
+            s_p = c.v;
+          }
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int l = s_l;
+        const double p = s_p;
+        // exchange column l with the boundary column m-1 in the panel (Sec. 2.4)
+        if (l != m - 1) {
+          for (int i = tid; i < bb; i += kBT) {
+            const T v = P[i * pw + l];
+            P[i * pw + l] = P[i * pw + m - 1];
+            P[i * pw + m - 1] = v;
+          }
+        }
+        __syncthreads();
+        // factor row t (Eq. (3), Sec. 2.3); the boundary keeps the pivot
+        for (int j = tid; j < m - 1; j += kBT) P[t * pw + j] = (T)((double)P[t * pw + j] / p);
+        __syncthreads();
+        // rank-1 update of the remaining panel rows (Eq. (2))
+        for (int e = tid; e < (bb - 1 - t) * (m - 1); e += kBT) {
+          const int i = t + 1 + e / (m - 1), j = e % (m - 1);
+          P[i * pw + j] = fma_t(-P[i * pw + m - 1], P[t * pw + j], P[i * pw + j]);
+        }
+        __syncthreads();
+      }
+      if (s_bad) break;
+      const int rows = n - s0 - bb;
+      if (rows <= 0) continue;
+      // compose the panel's column exchanges into a move list on <= 2 bb positions
+      if (tid == 0) {
+        int pos[2 * kKB], val[2 * kKB];
+        int np = 0;
+        for (int t = 0; t < bb; ++t) {
+          const int a = s_swap[t], b = m0 - 1 - t;
+          int ia = -1, ib = -1;
+          for (int k = 0; k < np; ++k) {
+            if (pos[k] == a) ia = k;
+            if (pos[k] == b) ib = k;
+          }
+          if (ia < 0) { pos[np] = a; val[np] = a; ia = np++; }
+          if (ib < 0) { pos[np] = b; val[np] = b; ib = np++; }
+          const int tmp = val[ia];
+          val[ia] = val[ib];
+          val[ib] = tmp;
+        }
+        int k2 = 0;
+        for (int k = 0; k < np; ++k)
+          if (pos[k] != val[k]) {
+            moved_dst[k2] = pos[k];
+            moved_src[k2] = val[k];
+            ++k2;
+          }
+        s_nmoved = k2;
+      }
+      __syncthreads();
+      const int nmoved = s_nmoved;
+      const int ncols = m0 - bb;
+      // trailing rows: one warp per row
+      for (int i = s0 + bb + warp; i < n; i += kBT / 32) {
+        T* row = W + (int64_t)i * ldw;
+        // column exchanges of the panel, composed
+        // (at most 2 * kKB = 32 positions move: one per lane)
+        T mv = T(0);
+        if (lane < nmoved) mv = row[moved_src[lane]];
+        __syncwarp();
+        if (lane < nmoved) row[moved_dst[lane]] = mv;
+        __syncwarp();
+        // multipliers: forward substitution with U[t'][t] = P[t'][m0-1-t]
+        T a = (lane < bb) ? row[m0 - 1 - lane] : T(0);
+        T cm[kKB];
+#pragma unroll
+        for (int t = 0; t < kKB; ++t) {
+          if (t < bb) {
+            const T ct = __shfl_sync(0xffffffffu, a, t);
+            cm[t] = ct;
+            if (lane > t && lane < bb) a = fma_t(-ct, P[t * pw + (m0 - 1 - lane)], a);
+          } else {
+            cm[t] = T(0);
+          }
+        }
+        // the panel's rank-1 updates, in pivot order, one register per element
+        for (int j = lane; j < ncols; j += 32) {
+          T v = row[j];
+#pragma unroll
+          for (int t = 0; t < kKB; ++t)
+            if (t < bb) v = fma_t(-cm[t], P[t * pw + j], v);
+          row[j] = v;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      flags = s_bad;
+      double sg, la;
+      if (flags & kFlagNaN) {
+        sg = la = __longlong_as_double(0x7ff8000000000000ULL);
+      } else if (flags & kFlagSingular) {
+        sg = 0.0;
+        la = -__longlong_as_double(0x7ff0000000000000ULL);
+      } else {
+        sg = sign;
+        la = sum + comp;
+      }
+      args.signs[mat] = sg;
+      args.logabs[mat] = la;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                      const int64_t* lda, int64_t count, int64_t n_max, double* signs,
+                      double* logabs, cudaStream_t stream) {
+  const int64_t ldw = (int64_t)align_up((size_t)std::max<int64_t>(n_max, 1), 4);
+  const size_t smem = (size_t)kKB * (n_max + 1) * sizeof(T) + (size_t)n_max * 4 + 4 * kKB * 4 + 64;
+  if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
+  static size_t smem_set[2] = {0, 0};
+  const int ti = sizeof(T) == 8;
+  if (smem > 48 * 1024 && smem_set[ti] < smem) {
+    if (cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return LD_ERR_CUDA;
+    smem_set[ti] = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, kBT, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  per_sm = std::min(per_sm, 4);
+  const int64_t grid = std::min<int64_t>((int64_t)device_sm_count() * per_sm, count);
+  const size_t ws_bytes = (size_t)grid * n_max * ldw * sizeof(T);
+  const size_t aux_bytes = align_up((size_t)count * 4, kAlign) + align_up((size_t)(n_max + 2) * 4, kAlign) + kAlign;
+  void* scratch = nullptr;
+  ld_status st = scratch_alloc(&scratch, align_up(ws_bytes, kAlign) + aux_bytes + kAlign, stream);
+  if (st != LD_OK) return st;
+  char* base = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
+  T* ws = reinterpret_cast<T*>(base);
+  char* p = base + align_up(ws_bytes, kAlign);
+  int* order = reinterpret_cast<int*>(p);
+  p += align_up((size_t)count * 4, kAlign);
+  int* hist = reinterpret_cast<int*>(p);
+  p += align_up((size_t)(n_max + 2) * 4, kAlign);
+  int* counter = reinterpret_cast<int*>(p);
+  {
+    ProfScope ps("batched_order", stream);
+    order_kernel<<<1, 1024, 0, stream>>>(n, (int)count, (int)n_max, order, counter, hist);
+  }
+  if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+  if (st == LD_OK) {
+    BatchedArgs a{A_ptrs, n, lda, (int)a_dtype, (int)count, (int)n_max, ldw, order, counter, signs, logabs};
+    ProfScope ps("batched", stream);
+    batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, ws);
+    if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+  }
+  scratch_free(scratch, stream);
+  return st;
+}
+
+}  // namespace
+
+}  // namespace ld
 
 extern "C" ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                                        const int64_t* lda, int64_t count, int64_t n_max,
                                        ld_mode mode, void* stream, double* signs, double* logabs) {
-  (void)A_ptrs; (void)a_dtype; (void)n; (void)lda; (void)count; (void)n_max; (void)mode;
-  (void)stream; (void)signs; (void)logabs;
-  return LD_ERR_UNSUPPORTED;
+  using namespace ld;
+  if (count < 0 || n_max < 0 || (count > 0 && (!A_ptrs || !n || !lda || !signs || !logabs)))
+    return LD_ERR_INVALID_ARG;
+  if (a_dtype != LD_DTYPE_F64 && a_dtype != LD_DTYPE_F32) return LD_ERR_INVALID_ARG;
+  if (mode != LD_F64_PLAIN && mode != LD_F32_PLAIN) return mode_valid(mode) ? LD_ERR_UNSUPPORTED : LD_ERR_INVALID_ARG;
+  if (count == 0) return LD_OK;
+  if (count > 0x7fffffff || n_max > 4096) return LD_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (mode == LD_F64_PLAIN)
+    return run_batched<double>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs, logabs, s);
+  return run_batched<float>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs, logabs, s);
 }

@@ -153,3 +153,26 @@ def dyadic_lu(n: int, seed: int, density: float = 0.3):
     det_sign = (-1.0 if inv % 2 else 1.0) * float(np.prod(np.sign(d)))
     logabs = n * math.log(8.0)
     return A, det_sign, logabs, perm.astype(np.int64)
+
+
+def batched_covariances_torch(sizes, seed: int = 3, ridge: float = 1e-2, device="cuda",
+                              dtype=None):
+    """GPU generator of one X^T X / (2n) + ridge * I matrix per size (X is 2n x n),
+    drawn per size class with a seeded torch.Generator; FP32 by default. Returns
+    the matrices in the order of ``sizes``."""
+    import torch
+
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    sizes = [int(x) for x in sizes]
+    out = [None] * len(sizes)
+    for n in sorted(set(sizes)):
+        idx = [i for i, x in enumerate(sizes) if x == n]
+        X = torch.randn(len(idx), 2 * n, n, generator=g, device=device, dtype=torch.float64)
+        S = torch.bmm(X.transpose(1, 2), X) / (2 * n)
+        S.diagonal(dim1=1, dim2=2).add_(ridge)
+        S = S.to(dtype)
+        for k, i in enumerate(idx):
+            out[i] = S[k].contiguous()
+    return out
