@@ -106,6 +106,8 @@ ld_status ld_logdet_factor(const void* A, ld_dtype a_dtype, int64_t n, int64_t l
  *   g        device pointer to one double (the incoming gradient of logabs)
  *   grad     device output, n x ldg row-major, element type of the mode's storage
  * The paper has no derivative; this is the chain rule applied to its output.
+ * Reads the record header first (a short synchronous copy on `stream`) and waits
+ * for `stream` before returning.
  */
 ld_status ld_logdet_backward(const void* factors, const double* g, void* grad, int64_t ldg,
                              void* stream);
@@ -125,6 +127,34 @@ ld_status ld_logdet_backward(const void* factors, const double* g, void* grad, i
 ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                             const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,
                             void* stream, double* signs, double* logabs);
+
+/*
+ * ld_logdet_batched_factor - as ld_logdet_batched, and keeps one factor record
+ * per matrix (the layout of ld_factors_size), for ld_logdet_backward_batched.
+ *   factors  device array of `count` device pointers; factors[i] is a 256-B
+ *            aligned buffer of ld_factors_size(n[i], mode) bytes
+ * The sweep runs in place in each record (no per-CTA workspace).
+ */
+ld_status ld_logdet_batched_factor(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                                   const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,
+                                   void* stream, void* const* factors, double* signs,
+                                   double* logabs);
+
+/*
+ * ld_logdet_backward_batched - G_i = g_i * A_i^{-T} for `count` factor records of
+ * one size n and one mode (written by ld_logdet_factor or
+ * ld_logdet_batched_factor), in one batched sequence of launches.
+ *   factors  device array of `count` record pointers (read only)
+ *   g        device array of `count` doubles (incoming gradients of logabs)
+ *   grads    device array of `count` device pointers; grads[i] is n x ldg
+ *            row-major in the storage type of the mode (FP64 or FP32)
+ * FP32 records: the block products run on the tensor cores in split TF32
+ * (hi*hi + hi*lo + lo*hi, FP32 accumulation); FP64 records: FP64 FMAs.
+ * Waits for `stream` before returning (to report LD_ERR_TIMEOUT).
+ */
+ld_status ld_logdet_backward_batched(const void* const* factors, int64_t count, int64_t n,
+                                     ld_mode mode, const double* g, void* const* grads,
+                                     int64_t ldg, void* stream);
 
 /*
  * Launch accounting for measurement (no counterpart in the paper). While on,

@@ -27,6 +27,9 @@ from ._lib import (  # noqa: F401
 from .api import (  # noqa: F401
     BatchedInputs,
     Factors,
+    LogAbsDet,
+    logabsdet,
+    logdet_backward,
     logdet,
     logdet_batched,
     logdet_factor,

@@ -49,6 +49,9 @@ SIGNATURES = {
     "ld_logdet_factor": ([_vp, _int, _i64, _i64, _int, _vp, _vp, _pd, _pd], _int),
     "ld_logdet_backward": ([_vp, _vp, _vp, _i64, _vp], _int),
     "ld_logdet_batched": ([_vp, _int, _vp, _vp, _i64, _i64, _int, _vp, _vp, _vp], _int),
+    "ld_logdet_batched_factor": ([_vp, _int, _vp, _vp, _i64, _i64, _int, _vp, _vp, _vp, _vp],
+                                 _int),
+    "ld_logdet_backward_batched": ([_vp, _i64, _i64, _int, _vp, _vp, _i64, _vp], _int),
     "ld_rankb_update": ([_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _int),
     "ld_profile_start": ([ctypes.c_char_p], _int),
     "ld_profile_stop": ([], _int),
@@ -121,6 +124,16 @@ def ld_logdet_backward(factors, g, grad, ldg, stream) -> int:
 def ld_logdet_batched(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream, signs, logabs) -> int:
     return load().ld_logdet_batched(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream, signs,
                                     logabs)
+
+
+def ld_logdet_batched_factor(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream, factors, signs,
+                             logabs) -> int:
+    return load().ld_logdet_batched_factor(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream,
+                                           factors, signs, logabs)
+
+
+def ld_logdet_backward_batched(factors, count, n, mode, g, grads, ldg, stream) -> int:
+    return load().ld_logdet_backward_batched(factors, count, n, mode, g, grads, ldg, stream)
 
 
 def ld_rankb_update(mode, M, N, K, A, lda, B, ldb, D, ldd, stream) -> int:

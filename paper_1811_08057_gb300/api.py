@@ -155,3 +155,90 @@ def logdet_batched(batch, mode="f32_plain", stream=None, out=None):
                                   logabs.data_ptr())
     _lib.check("ld_logdet_batched", code)
     return signs, logabs
+
+
+def _aligned_records(sizes, mode, device):
+    """One contiguous buffer holding a 256-B aligned factor record per size."""
+    offs, total = [], 0
+    for n in sizes:
+        total = _align(total)
+        offs.append(total)
+        total += _lib.ld_factors_size(int(n), mode)
+    buf = torch.empty(total + 256, dtype=torch.uint8, device=device)
+    shift = (-buf.data_ptr()) % 256
+    buf = buf[shift:shift + total]
+    return buf, offs
+
+
+def logdet_backward(f: Factors, g=1.0, stream=None) -> torch.Tensor:
+    """G = g * A^{-T} from a factor record (ld_logdet_backward)."""
+    dev = f.record.device
+    gt = torch.as_tensor(g, dtype=torch.float64, device=dev).reshape(1).contiguous()
+    dt = torch.float64 if f.mode in (_lib.LD_F64_PLAIN, _lib.LD_F64_BLOCKED) else torch.float32
+    G = torch.empty(f.n, f.n, dtype=dt, device=dev)
+    code = _lib.ld_logdet_backward(f.record.data_ptr(), gt.data_ptr(), G.data_ptr(), max(f.n, 1),
+                                   _stream_handle(stream))
+    _lib.check("ld_logdet_backward", code)
+    return G
+
+
+class LogAbsDet(torch.autograd.Function):
+    """log|det A| with gradient g * A^{-T}, both through liblogdet.
+
+    Single matrix (n x n) or a batch (B x n x n, one size). Forward keeps the
+    factor records (ld_logdet_factor, or ld_logdet_batched_factor for a batch);
+    backward runs ld_logdet_backward_batched on them.
+    """
+
+    @staticmethod
+    def forward(ctx, A, mode="f32_plain"):
+        mode_c = _mode_code(mode)
+        batched = A.dim() == 3
+        mats = list(A) if batched else [A]
+        n = A.shape[-1]
+        dev = A.device
+        if batched:
+            if mode_c not in (_lib.LD_F64_PLAIN, _lib.LD_F32_PLAIN):
+                raise ValueError("batched forward supports f64_plain / f32_plain")
+            mats = [M.contiguous() for M in mats]
+            batch = BatchedInputs(mats)
+            buf, offs = _aligned_records([n] * len(mats), mode_c, dev)
+            recs = torch.tensor([buf.data_ptr() + o for o in offs], dtype=torch.int64, device=dev)
+            signs = torch.empty(len(mats), dtype=torch.float64, device=dev)
+            logabs = torch.empty(len(mats), dtype=torch.float64, device=dev)
+            code = _lib.ld_logdet_batched_factor(batch.ptrs.data_ptr(), batch.dtype_code,
+                                                 batch.n.data_ptr(), batch.lda.data_ptr(),
+                                                 batch.count, batch.n_max, mode_c,
+                                                 _stream_handle(None), recs.data_ptr(),
+                                                 signs.data_ptr(), logabs.data_ptr())
+            _lib.check("ld_logdet_batched_factor", code)
+            ctx.keep = (buf, recs, batch)
+            out = logabs
+        else:
+            f = logdet_factor(A.contiguous(), mode_c)
+            recs = torch.tensor([f.record.data_ptr()], dtype=torch.int64, device=dev)
+            ctx.keep = (f.record, recs, None)
+            out = f.logabs.reshape(())
+        ctx.meta = (batched, n, mode_c, A.dtype, len(mats))
+        return out.to(A.dtype) if A.dtype == torch.float32 else out.clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        batched, n, mode_c, dtype, count = ctx.meta
+        _, recs, _ = ctx.keep
+        dev = grad_out.device
+        g = grad_out.detach().to(torch.float64).reshape(count).contiguous()
+        sdt = torch.float64 if mode_c in (_lib.LD_F64_PLAIN, _lib.LD_F64_BLOCKED) else torch.float32
+        G = torch.empty(count, n, n, dtype=sdt, device=dev)
+        gptrs = torch.tensor([G[i].data_ptr() for i in range(count)], dtype=torch.int64,
+                             device=dev)
+        code = _lib.ld_logdet_backward_batched(recs.data_ptr(), count, n, mode_c, g.data_ptr(),
+                                               gptrs.data_ptr(), n, _stream_handle(None))
+        _lib.check("ld_logdet_backward_batched", code)
+        G = G.to(dtype)
+        return (G if batched else G[0]), None
+
+
+def logabsdet(A: torch.Tensor, mode="f32_plain") -> torch.Tensor:
+    """Differentiable log|det A| (n x n or B x n x n) through liblogdet."""
+    return LogAbsDet.apply(A, mode)

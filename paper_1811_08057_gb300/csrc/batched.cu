@@ -38,6 +38,8 @@ struct BatchedArgs {
   int* counter;
   double* signs;
   double* logabs;
+  void* const* factors;  // optional: one factor record per matrix (else nullptr)
+  int mode;
 };
 
 // Counting sort of the matrix indices by decreasing size (one CTA).
@@ -91,8 +93,8 @@ __global__ void __launch_bounds__(kBT)
   __shared__ int s_swap[kKB];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T* W = ws + (int64_t)blockIdx.x * n_max * args.ldw;
-  const int64_t ldw = args.ldw;
+  T* const ws_W = ws ? ws + (int64_t)blockIdx.x * n_max * args.ldw : nullptr;
+  const int64_t ws_ldw = args.ldw;
 
   while (true) {
     if (tid == 0) {
@@ -115,6 +117,21 @@ __global__ void __launch_bounds__(kBT)
     const int n = (int)n64;
     const int64_t lda = args.lda[mat];
     const void* A = args.A_ptrs[mat];
+    // factor mode: sweep in place in the matrix's own record (layout of ld_factors_size)
+    char* rec = args.factors ? static_cast<char*>(args.factors[mat]) : nullptr;
+    const int64_t ldw = rec ? (int64_t)align_up((size_t)n, 32) : ws_ldw;
+    T* W = rec ? reinterpret_cast<T*>(rec + kAlign) : ws_W;
+    int* rec_colperm = nullptr;
+    int* rec_pivpos = nullptr;
+    double* rec_pivval = nullptr;
+    if (rec) {
+      char* q = rec + kAlign + align_up((size_t)n * ldw * sizeof(T), kAlign);
+      rec_colperm = reinterpret_cast<int*>(q);
+      q += align_up((size_t)n * 4, kAlign);
+      rec_pivpos = reinterpret_cast<int*>(q);
+      q += align_up((size_t)n * 4, kAlign);
+      rec_pivval = reinterpret_cast<double*>(q);
+    }
     // stage the matrix into the CTA's workspace (a0)
     for (int64_t e = tid; e < (int64_t)n * n; e += kBT) {
       const int i = (int)(e / n), j = (int)(e % n);
@@ -165,6 +182,10 @@ __global__ void __launch_bounds__(kBT)
             s_swap[t] = l;
             s_l = l;
             s_p = c.v;
+            if (rec) {
+              rec_pivpos[s0 + t] = l;
+              rec_pivval[s0 + t] = c.v;
+            }
           }
         }
         __syncthreads();
@@ -191,8 +212,15 @@ __global__ void __launch_bounds__(kBT)
         __syncthreads();
       }
       if (s_bad) break;
+      if (rec) {
+        // the panel rows are final: factored rows r, pivots and multipliers
+        for (int e = tid; e < bb * m0; e += kBT) {
+          const int t = e / m0, j = e % m0;
+          W[(int64_t)(s0 + t) * ldw + j] = P[t * pw + j];
+        }
+      }
       const int rows = n - s0 - bb;
-      if (rows <= 0) continue;
+      if (rows <= 0 && !rec) continue;
       // compose the panel's column exchanges into a move list on <= 2 bb positions
       if (tid == 0) {
         int pos[2 * kKB], val[2 * kKB];
@@ -222,6 +250,18 @@ __global__ void __launch_bounds__(kBT)
       __syncthreads();
       const int nmoved = s_nmoved;
       const int ncols = m0 - bb;
+      if (rec) {
+        // earlier (frozen) rows keep the layout of the record: the panel's
+        // column exchanges reach them too
+        for (int i = warp; i < s0; i += kBT / 32) {
+          T* row = W + (int64_t)i * ldw;
+          T mv = T(0);
+          if (lane < nmoved) mv = row[moved_src[lane]];
+          __syncwarp();
+          if (lane < nmoved) row[moved_dst[lane]] = mv;
+          __syncwarp();
+        }
+      }
       // trailing rows: one warp per row
       for (int i = s0 + bb + warp; i < n; i += kBT / 32) {
         T* row = W + (int64_t)i * ldw;
@@ -245,6 +285,7 @@ __global__ void __launch_bounds__(kBT)
             cm[t] = T(0);
           }
         }
+        if (rec && lane < bb) row[m0 - 1 - lane] = a;  // multipliers (L) of this panel
         // the panel's rank-1 updates, in pivot order, one register per element
         for (int j = lane; j < ncols; j += 32) {
           T v = row[j];
@@ -270,7 +311,18 @@ __global__ void __launch_bounds__(kBT)
       }
       args.signs[mat] = sg;
       args.logabs[mat] = la;
+      if (rec) {
+        RecordHeader* h = reinterpret_cast<RecordHeader*>(rec);
+        h->n = n;
+        h->ldf = ldw;
+        h->mode = args.mode;
+        h->flags = flags;
+        h->sign = sg;
+        h->logabs = la;
+      }
     }
+    if (rec)
+      for (int j = tid; j < n; j += kBT) rec_colperm[j] = label[j];
     __syncthreads();
   }
 }
@@ -278,7 +330,7 @@ __global__ void __launch_bounds__(kBT)
 template <typename T>
 ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                       const int64_t* lda, int64_t count, int64_t n_max, double* signs,
-                      double* logabs, cudaStream_t stream) {
+                      double* logabs, void* const* factors, ld_mode mode, cudaStream_t stream) {
   const int64_t ldw = (int64_t)align_up((size_t)std::max<int64_t>(n_max, 1), 4);
   const size_t smem = (size_t)kKB * (n_max + 1) * sizeof(T) + (size_t)n_max * 4 + 4 * kKB * 4 + 64;
   if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
@@ -297,7 +349,7 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
     per_sm = 1;
   per_sm = std::min(per_sm, 4);
   const int64_t grid = std::min<int64_t>((int64_t)device_sm_count() * per_sm, count);
-  const size_t ws_bytes = (size_t)grid * n_max * ldw * sizeof(T);
+  const size_t ws_bytes = factors ? 0 : (size_t)grid * n_max * ldw * sizeof(T);
   const size_t aux_bytes = align_up((size_t)count * 4, kAlign) + align_up((size_t)(n_max + 2) * 4, kAlign) + kAlign;
   void* scratch = nullptr;
   ld_status st = scratch_alloc(&scratch, align_up(ws_bytes, kAlign) + aux_bytes + kAlign, stream);
@@ -316,9 +368,10 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   }
   if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   if (st == LD_OK) {
-    BatchedArgs a{A_ptrs, n, lda, (int)a_dtype, (int)count, (int)n_max, ldw, order, counter, signs, logabs};
+    BatchedArgs a{A_ptrs, n,      lda,    (int)a_dtype, (int)count, (int)n_max, ldw,
+                  order,  counter, signs, logabs,       factors,    (int)mode};
     ProfScope ps("batched", stream);
-    batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, ws);
+    batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, factors ? nullptr : ws);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   scratch_free(scratch, stream);
@@ -329,9 +382,9 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
 
 }  // namespace ld
 
-extern "C" ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
-                                       const int64_t* lda, int64_t count, int64_t n_max,
-                                       ld_mode mode, void* stream, double* signs, double* logabs) {
+static ld_status batched_entry(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                               const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,
+                               void* stream, void* const* factors, double* signs, double* logabs) {
   using namespace ld;
   if (count < 0 || n_max < 0 || (count > 0 && (!A_ptrs || !n || !lda || !signs || !logabs)))
     return LD_ERR_INVALID_ARG;
@@ -341,6 +394,23 @@ extern "C" ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dty
   if (count > 0x7fffffff || n_max > 4096) return LD_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (mode == LD_F64_PLAIN)
-    return run_batched<double>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs, logabs, s);
-  return run_batched<float>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs, logabs, s);
+    return run_batched<double>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs,
+                               logabs, factors, mode, s);
+  return run_batched<float>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs,
+                            logabs, factors, mode, s);
+}
+
+extern "C" ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                                       const int64_t* lda, int64_t count, int64_t n_max,
+                                       ld_mode mode, void* stream, double* signs, double* logabs) {
+  return batched_entry(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream, nullptr, signs, logabs);
+}
+
+extern "C" ld_status ld_logdet_batched_factor(const void* const* A_ptrs, ld_dtype a_dtype,
+                                              const int64_t* n, const int64_t* lda, int64_t count,
+                                              int64_t n_max, ld_mode mode, void* stream,
+                                              void* const* factors, double* signs,
+                                              double* logabs) {
+  if (count > 0 && !factors) return LD_ERR_INVALID_ARG;
+  return batched_entry(A_ptrs, a_dtype, n, lda, count, n_max, mode, stream, factors, signs, logabs);
 }

@@ -43,7 +43,8 @@ template <int KIND>
 __global__ void __launch_bounds__(128, 1)
     rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                    float* __restrict__ D, int64_t ldd, int M, int N, int K, int* __restrict__ err) {
+                    float* __restrict__ D, int64_t ldd, int64_t dstride, int M, int N, int K,
+                    int* __restrict__ err) {
   using C = TcCfg<KIND>;
   constexpr uint32_t IDESC = tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, C::BM, C::BN);
   extern __shared__ uint8_t smem_raw[];
@@ -56,7 +57,9 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * C::BN;
+  const int z = blockIdx.z;  // batch index (one matrix per z)
   const int nk = K / C::BK;
+  D += (int64_t)z * dstride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -85,11 +88,11 @@ __global__ void __launch_bounds__(128, 1)
       if (!tc::mbar_wait(&empty[s], (r & 1) ^ 1, err)) break;
       uint8_t* st = smem + s * C::STAGE_BYTES;
       tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-      tc::tma_load_2d(st, &mAh, &full[s], kc * C::BK, m0);
-      tc::tma_load_2d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0);
+      tc::tma_load_3d(st, &mAh, &full[s], kc * C::BK, m0, z);
+      tc::tma_load_3d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0, z);
       if (C::NT == 2) {
-        tc::tma_load_2d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0);
-        tc::tma_load_2d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0);
+        tc::tma_load_3d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0, z);
+        tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0, z);
       }
       ++issued;
     }
@@ -258,32 +261,43 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// K-major operand (rows x K, compact) as a TMA map with 128-byte swizzled
-// boxes of box_rows rows.
-bool make_map(CUtensorMap* map, const void* base, int rows, int K, int es, int box_rows) {
+}  // namespace
+
+// K-major operand as a 3-D TMA map: `batch` matrices `bstride` elements apart,
+// each rows x K with leading dimension ld (elements), boxes of 128 bytes x
+// box_rows rows with the 128-byte swizzle. Loads past rows / K read zeros.
+bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, int batch,
+              int64_t bstride, int es, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((size_t)K * es) % 16 != 0) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)K * es};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((size_t)ld * es) % 16 != 0 ||
+      ((size_t)bstride * es) % 16 != 0)
+    return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * es,
+                           (cuuint64_t)(batch > 1 ? bstride : (int64_t)rows * ld) * es};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                   2, const_cast<void*>(base), dims, strides, box, estr,
+                   3, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
+namespace {
+
 template <int KIND>
-ld_status launch_tc(const void* ah, const void* al, const void* bh, const void* bl, int M, int N,
-                    int K, float* D, int64_t ldd, int* err, cudaStream_t stream) {
+ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K, float* D,
+                    int64_t ldd, int64_t dstride, int batch, int* err, cudaStream_t stream) {
   using C = TcCfg<KIND>;
   CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, ah, M, K, C::ES, C::BM) || !make_map(&mBh, bh, N, K, C::ES, C::BN))
+  if (!make_map(&mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+      !make_map(&mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
     return LD_ERR_CUDA;
   if (C::NT == 2) {
-    if (!make_map(&mAl, al, M, K, C::ES, C::BM) || !make_map(&mBl, bl, N, K, C::ES, C::BN))
+    if (!make_map(&mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+        !make_map(&mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
       return LD_ERR_CUDA;
   } else {
     mAl = mAh;
@@ -296,9 +310,10 @@ ld_status launch_tc(const void* ah, const void* al, const void* bh, const void* 
       return LD_ERR_CUDA;
     attr_set = true;
   }
-  dim3 grid((unsigned)ceil_div(N, C::BN), (unsigned)ceil_div(M, C::BM));
+  dim3 grid((unsigned)ceil_div(N, C::BN), (unsigned)ceil_div(M, C::BM), (unsigned)batch);
   ProfScope ps("rankb_tc", stream);
-  rankb_tc_kernel<KIND><<<grid, 128, C::SMEM, stream>>>(mAh, mAl, mBh, mBl, D, ldd, M, N, K, err);
+  rankb_tc_kernel<KIND><<<grid, 128, C::SMEM, stream>>>(mAh, mAl, mBh, mBl, D, ldd, dstride, M, N,
+                                                        K, err);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }
@@ -370,13 +385,26 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
   LD_CHECK_LAUNCH();
   float* Df = static_cast<float*>(D);
   if ((ldd % 4) != 0 || (reinterpret_cast<uintptr_t>(D) & 15) != 0) return LD_ERR_UNSUPPORTED;
+  const TcOperand oa{ah, al, K, 0}, ob{bh, bl, K, 0};
+  return rankb_tc(mode, oa, ob, (int)M, (int)N, (int)K, Df, ldd, 0, 1, err, stream);
+}
+
+// Tensor-core update on operands already in the mode's format (hi / lo parts),
+// batched over `batch` matrices (operand and D strides in elements).
+ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, int N, int K,
+                   float* D, int64_t ldd, int64_t dstride, int batch, int* err,
+                   cudaStream_t stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return LD_OK;
+  if (K % 64 != 0 || (ldd % 4) != 0 || (dstride % 4) != 0 ||
+      (reinterpret_cast<uintptr_t>(D) & 15) != 0)
+    return LD_ERR_UNSUPPORTED;
   switch (mode) {
     case LD_F32_TF32:
-      return launch_tc<kTF32>(ah, nullptr, bh, nullptr, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+      return launch_tc<kTF32>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
     case LD_F32_3XTF32:
-      return launch_tc<kTF32x3>(ah, al, bh, bl, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+      return launch_tc<kTF32x3>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
     case LD_F32_BF16X3:
-      return launch_tc<kBF16x3>(ah, al, bh, bl, (int)M, (int)N, (int)K, Df, ldd, err, stream);
+      return launch_tc<kBF16x3>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
     default:
       return LD_ERR_INVALID_ARG;
   }

@@ -9,7 +9,7 @@ constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
 constexpr int kCandCols = 512;      // narrowest column tile of a candidate (FP64: 256 x double2)
 constexpr size_t kAlign = 256;
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 inline bool mode_valid(int mode) { return mode >= LD_F64_PLAIN && mode <= LD_F32_BF16X3; }
@@ -117,6 +117,17 @@ ld_status scratch_alloc(void** p, size_t bytes, cudaStream_t stream);
 void scratch_free(void* p, cudaStream_t stream);
 
 // ---- tensor-core / FP64 rank-b update (gemm_tc.cu) ----
+// One operand of the tensor-core update: hi (and, for split modes, lo) parts,
+// rows of K elements `ld` apart, matrices `bstride` elements apart.
+struct TcOperand {
+  const void* hi;
+  const void* lo;
+  int64_t ld;
+  int64_t bstride;
+};
+ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, int N, int K,
+                   float* D, int64_t ldd, int64_t dstride, int batch, int* err,
+                   cudaStream_t stream);
 size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K);
 ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                        const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
