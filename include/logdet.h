@@ -170,6 +170,11 @@ ld_status ld_logdet_backward_batched(const void* const* factors, int64_t count, 
 ld_status ld_profile_start(const char* kernel);
 ld_status ld_profile_stop(void);
 ld_status ld_profile_query(const char* kernel, int64_t* launches, double* total_ms);
+/* Algorithmic DRAM bytes and useful flops of class `kernel` (NULL = all) since
+ * ld_profile_start, as declared by each launch (the roofline numerators). */
+ld_status ld_profile_work(const char* kernel, double* bytes, double* flops);
+/* Comma-separated names of the kernel classes launched since ld_profile_start. */
+ld_status ld_profile_classes(char* buf, int64_t cap);
 
 /*
  * ld_rankb_update - the trailing update of the blocked sweep on its own:

@@ -56,6 +56,8 @@ SIGNATURES = {
     "ld_profile_start": ([ctypes.c_char_p], _int),
     "ld_profile_stop": ([], _int),
     "ld_profile_query": ([ctypes.c_char_p, _vp, _vp], _int),
+    "ld_profile_work": ([ctypes.c_char_p, _vp, _vp], _int),
+    "ld_profile_classes": ([_vp, _i64], _int),
     "ld_status_string": ([_int], ctypes.c_char_p),
     "ld_version": ([], ctypes.c_char_p),
 }
@@ -156,6 +158,23 @@ def ld_profile_query(kernel=None):
                                    ctypes.addressof(t))
     check("ld_profile_query", code)
     return n.value, t.value
+
+
+def ld_profile_work(kernel=None):
+    """(bytes, flops) declared by the launches of a kernel class since ld_profile_start."""
+    b = ctypes.c_double()
+    f = ctypes.c_double()
+    code = load().ld_profile_work(kernel.encode() if kernel else None, ctypes.addressof(b),
+                                  ctypes.addressof(f))
+    check("ld_profile_work", code)
+    return b.value, f.value
+
+
+def ld_profile_classes():
+    buf = ctypes.create_string_buffer(4096)
+    check("ld_profile_classes", load().ld_profile_classes(ctypes.addressof(buf), 4096))
+    v = buf.value.decode()
+    return [x for x in v.split(",") if x]
 
 
 def ld_status_string(code) -> str:

@@ -225,7 +225,7 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
   {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(np * np, 256), sm * 4 / std::max<int64_t>(1, count) + 1)),
               (unsigned)count);
-    ProfScope ps("bwd_unpack", stream);
+    ProfScope ps("bwd_unpack", stream, (double)count * np * np * sizeof(T) * (parts + 1), 0.0);
     // unpack_kernel indexes with np*np per matrix; bstride equals np*np because
     // np*np*sizeof(T) is a multiple of 256 bytes (np is a multiple of 128)
     unpack_kernel<T, SPLIT><<<grid, 256, 0, stream>>>(recs, (int)n, (int)np, ldf, Lh, Ll, Uh, Ul,
@@ -241,7 +241,9 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
                       reinterpret_cast<float*>(Yv + d_off), np, bstride, (int)count, err, stream);
     }
     dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64), (unsigned)count);
-    ProfScope ps("rankb_f64", stream);
+    ProfScope ps("rankb_f64", stream,
+                 (double)count * (16.0 * M * N + 8.0 * (double)(M + N) * K),
+                 (double)count * 2.0 * M * N * K);
     rankb_f64_batched_kernel<<<grid, 256, 0, stream>>>(
         reinterpret_cast<const double*>(Ah + a_off), np, reinterpret_cast<const double*>(Bh + b_off),
         np, reinterpret_cast<double*>(Yv + d_off), np, bstride, (int)M, (int)N, (int)K);
@@ -257,7 +259,8 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
   }
   auto solve = [&](int I, int64_t M, bool lower) -> ld_status {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M, 8), 64)), (unsigned)count);
-    ProfScope ps("bwd_rowsolve", stream);
+    ProfScope ps("bwd_rowsolve", stream, (double)count * M * kNB * sizeof(T) * (SPLIT ? 4.0 : 2.0),
+                 (double)count * M * kNB * kNB);
     if (lower)
       rowsolve_kernel<T, true, SPLIT><<<grid, 256, solve_smem, stream>>>(recs, (int)n, (int)np, ldf,
                                                                          I, (int)M, Yv, Yh, Yl);
@@ -283,7 +286,7 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
   if (st == LD_OK) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n * n, 256), 1024)),
               (unsigned)count);
-    ProfScope ps("bwd_gather", stream);
+    ProfScope ps("bwd_gather", stream, (double)count * n * n * 2.0 * sizeof(T), 0.0);
     gather_kernel<T><<<grid, 256, 0, stream>>>(recs, grads, g, (int)n, (int)np, ldg, Yv);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }

@@ -136,7 +136,7 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     {
       const int warps = 8;
       const int grid = (int)std::min<int64_t>(ceil_div(rows, warps), device_sm_count() * 2);
-      ProfScope ps("trsm", stream);
+      ProfScope ps("trsm", stream, 3.0 * es * (double)rows * bb, (double)rows * bb * bb);
       trsm_kernel<T, kPanel / 32><<<grid, 256, trsm_smem, stream>>>(
           F, r.ldf, (int)n, (int)s0, (int)bb, (int)m0, (int)(s0 + bb), Cn);
     }
@@ -146,7 +146,7 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     }
     {
       dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(bb, 32));
-      ProfScope ps("transpose", stream);
+      ProfScope ps("transpose", stream, 2.0 * es * (double)rows * bb, 0.0);
       transpose_rows_kernel<T><<<grid, 256, 0, stream>>>(F, r.ldf, (int)s0, (int)bb, (int)rows, Rt);
     }
     if (cudaGetLastError() != cudaSuccess) {

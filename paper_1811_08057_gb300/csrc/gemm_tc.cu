@@ -311,7 +311,9 @@ ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K,
     attr_set = true;
   }
   dim3 grid((unsigned)ceil_div(N, C::BN), (unsigned)ceil_div(M, C::BM), (unsigned)batch);
-  ProfScope ps("rankb_tc", stream);
+  ProfScope ps("rankb_tc", stream,
+               (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),
+               (double)batch * 2.0 * M * N * K);
   rankb_tc_kernel<KIND><<<grid, 128, C::SMEM, stream>>>(mAh, mAl, mBh, mBl, D, ldd, dstride, M, N,
                                                         K, err);
   LD_CHECK_LAUNCH();
@@ -338,7 +340,8 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
   if (M <= 0 || N <= 0 || K <= 0) return LD_OK;
   if (mode == LD_F64_BLOCKED) {
     dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
-    ProfScope ps("rankb_f64", stream);
+    ProfScope ps("rankb_f64", stream, 16.0 * M * N + 8.0 * (double)(M + N) * K,
+                 2.0 * (double)M * N * K);
     rankb_f64_kernel<<<grid, 256, 0, stream>>>(static_cast<const double*>(A), lda,
                                                static_cast<const double*>(B), ldb,
                                                static_cast<double*>(D), ldd, (int)M, (int)N, (int)K);
@@ -360,7 +363,7 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
   const int gA = (int)std::min<int64_t>(sm * 4, ceil_div(M * K, 256));
   const int gB = (int)std::min<int64_t>(sm * 4, ceil_div(N * K, 256));
   {
-    ProfScope ps("split", stream);
+    ProfScope ps("split", stream, (double)(M + N) * K * (4.0 + (two ? 2.0 : 1.0) * es), 0.0);
     if (mode == LD_F32_BF16X3) {
       split_kernel<kBF16x3, __nv_bfloat16><<<gA, 256, 0, stream>>>(
           static_cast<const float*>(A), lda, (int)M, (int)K, reinterpret_cast<__nv_bfloat16*>(ah),

@@ -306,7 +306,8 @@ ld_status launch_stage(const void* A, ld_dtype a_dtype, int64_t lda, const Recor
   const int rows_per = (int)ceil_div(n, nrg);
   nrg = (int)ceil_div(n, rows_per);
   dim3 grid(nc, nrg);
-  ProfScope ps("stage", stream);
+  ProfScope ps("stage", stream,
+               (double)n * n * ((a_dtype == LD_DTYPE_F64 ? 8.0 : 4.0) + sizeof(T)), 0.0);
   if (a_dtype == LD_DTYPE_F64)
     stage_kernel<T, double><<<grid, kThreads, 0, stream>>>(
         static_cast<const double*>(A), lda, static_cast<T*>(r.F), r.ldf, n, rows_per, r.colperm,
@@ -330,7 +331,8 @@ ld_status launch_pivot_factor(const Record& r, int64_t s, int64_t swap_row_begin
   const int64_t n = r.n, m = n - s;
   const int64_t span = std::max<int64_t>(m, n - swap_row_begin);
   const int blocks = (int)std::max<int64_t>(1, ceil_div(span, kThreads));
-  ProfScope ps("pivot_factor", stream);
+  ProfScope ps("pivot_factor", stream,
+               (double)sizeof(T) * (2.0 * m + 4.0 * (double)(n - swap_row_begin)), (double)m);
   pivot_factor_kernel<T><<<blocks, kThreads, 0, stream>>>(
       static_cast<T*>(r.F), r.ldf, (int)n, (int)s, (int)swap_row_begin, r.colperm, r.pivpos,
       r.pivval, r.state, r.cand, ncand_for<T>(m));
@@ -350,7 +352,8 @@ ld_status launch_update(const Record& r, int64_t s, int64_t row_end, bool lookah
   const int64_t rows_per = ceil_div(rows, nrg);
   nrg = ceil_div(rows, rows_per);
   dim3 grid(nc, (unsigned)nrg);
-  ProfScope ps("update", stream);
+  ProfScope ps("update", stream, 2.0 * sizeof(T) * (double)rows * (double)(m - 1),
+               2.0 * (double)rows * (double)(m - 1));
   update_kernel<T, 4><<<grid, kThreads, 0, stream>>>(static_cast<T*>(r.F), r.ldf, (int)s, (int)m,
                                                      (int)row_end, (int)rows_per, r.colperm,
                                                      r.cand, lookahead ? 1 : 0);
@@ -361,7 +364,7 @@ ld_status launch_update(const Record& r, int64_t s, int64_t row_end, bool lookah
 template <typename T>
 ld_status launch_row_argmax(const Record& r, int64_t row, int64_t m, cudaStream_t stream) {
   const int nc = (int)std::max<int64_t>(1, ceil_div(m, col_tile(Vec<T>::N)));
-  ProfScope ps("row_argmax", stream);
+  ProfScope ps("row_argmax", stream, (double)sizeof(T) * m, 0.0);
   row_argmax_kernel<T><<<nc, kThreads, 0, stream>>>(static_cast<const T*>(r.F), r.ldf, (int)row,
                                                     (int)m, r.colperm, r.cand);
   LD_CHECK_LAUNCH();

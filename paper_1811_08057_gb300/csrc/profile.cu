@@ -1,6 +1,8 @@
 // Launch counting and CUDA-event timing per kernel class (ld_profile_* entry points).
 #include <string.h>
 
+#include <algorithm>
+
 #include <map>
 #include <mutex>
 #include <string>
@@ -27,6 +29,8 @@ struct Profiler {
   std::map<std::string, long long> launches;
   std::map<std::string, double> ms;
   std::map<std::string, long long> timed;
+  std::map<std::string, double> bytes;
+  std::map<std::string, double> flops;
 };
 
 Profiler& prof() {
@@ -45,11 +49,14 @@ cudaEvent_t take_event(Profiler& p, size_t idx) {
 
 }  // namespace
 
-ProfScope::ProfScope(const char* name, cudaStream_t stream) : slot_(-1), stream_(stream) {
+ProfScope::ProfScope(const char* name, cudaStream_t stream, double bytes, double flops)
+    : slot_(-1), stream_(stream) {
   Profiler& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
   if (!p.on) return;
   p.launches[name] += 1;
+  p.bytes[name] += bytes;
+  p.flops[name] += flops;
   if (!p.filter.empty() && p.filter != name) return;
   const size_t k = p.slots.size();
   cudaEvent_t a = take_event(p, 2 * k), b = take_event(p, 2 * k + 1);
@@ -81,6 +88,8 @@ ld_status ld_profile_start(const char* kernel) {
   p.launches.clear();
   p.ms.clear();
   p.timed.clear();
+  p.bytes.clear();
+  p.flops.clear();
   return LD_OK;
 }
 
@@ -121,6 +130,39 @@ ld_status ld_profile_query(const char* kernel, int64_t* launches, double* total_
     if (!kernel || kv.first == kernel) t += kv.second;
   *launches = n;
   *total_ms = t;
+  return LD_OK;
+}
+
+// Algorithmic bytes and flops summed over the launches of class `kernel` (NULL =
+// all classes) since ld_profile_start.
+ld_status ld_profile_work(const char* kernel, double* bytes, double* flops) {
+  if (!bytes || !flops) return LD_ERR_INVALID_ARG;
+  ld::Profiler& p = ld::prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  double b = 0.0, f = 0.0;
+  for (auto& kv : p.bytes)
+    if (!kernel || kv.first == kernel) b += kv.second;
+  for (auto& kv : p.flops)
+    if (!kernel || kv.first == kernel) f += kv.second;
+  *bytes = b;
+  *flops = f;
+  return LD_OK;
+}
+
+// Names of the kernel classes seen since ld_profile_start, comma-separated, into
+// buf (truncated to cap bytes including the terminator).
+ld_status ld_profile_classes(char* buf, int64_t cap) {
+  if (!buf || cap <= 0) return LD_ERR_INVALID_ARG;
+  ld::Profiler& p = ld::prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  std::string out;
+  for (auto& kv : p.launches) {
+    if (!out.empty()) out += ",";
+    out += kv.first;
+  }
+  const size_t k = std::min<size_t>(out.size(), (size_t)cap - 1);
+  memcpy(buf, out.data(), k);
+  buf[k] = 0;
   return LD_OK;
 }
 
