@@ -30,11 +30,8 @@ UNIT = "TFLOP/s"
 N_DEFAULT = 8000
 SEED = 1
 
-# dominant kernel per mode: (profile class, bound, algorithmic bytes per element update)
-DOMINANT = {
-    "f64_plain": ("update", "hbm", 16),
-    "f32_plain": ("update", "hbm", 8),
-}
+# nominal dense tensor rates relative to BF16 (TF32 1.1 / BF16 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
 DTYPE = {"f64_plain": "f64", "f32_plain": "f32", "f64_blocked": "f64", "f32_tf32": "f32+tf32",
          "f32_3xtf32": "f32+3xtf32", "f32_bf16x3": "f32+bf16x3"}
 
@@ -163,6 +160,110 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ rooflines
+def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
+    peaks = read_peaks()
+    sec = k_ms * 1e-3
+    out = {"kernel": kernel, "traffic": None, "peak_source": peaks["source"],
+           "kernel_ms_per_step": k_ms / steps, "kernel_launches_per_step": k_launches / steps,
+           "algorithmic_bytes_per_step": k_bytes / steps,
+           "algorithmic_flops_per_step": k_flops / steps}
+    if kernel == "rankb_tc":
+        # tensor-bound contraction; split modes run 3 products per useful flop
+        bf16 = peaks["bf16_tflops_sustained"]
+        if mode == "f32_bf16x3":
+            peak, note = bf16 / 3.0, "BF16 sustained / 3 (three products)"
+        elif mode == "f32_3xtf32":
+            peak, note = bf16 * TF32_OVER_BF16 / 3.0, "BF16 sustained x 1.1/2.25 (TF32) / 3"
+        else:
+            peak, note = bf16 * TF32_OVER_BF16, "BF16 sustained x 1.1/2.25 (TF32)"
+        ach = k_flops / sec / 1e12 if sec > 0 else None
+        out.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak if ach else None, "peak_note": note})
+        hbm = k_bytes / sec / 1e9 if sec > 0 else None
+        out["hbm_gbs_same_kernel"] = hbm
+    else:
+        ach = k_bytes / sec / 1e9 if sec > 0 else None
+        peak = peaks["hbm_gbs"]
+        out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak if ach else None})
+    return out
+
+
+def time_call(fn, warmup, steps, dev):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        r = fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps, r
+
+
+def other_paths(pk, _lib, A, main_mode, dev, err_gold=None):
+    """Quick timings of the other paths (each entry independent; errors recorded)."""
+    import torch
+    import workloads
+    res = {}
+    N = A.shape[0]
+    g = None
+    if err_gold and os.path.exists(err_gold):
+        with open(err_gold) as f:
+            g = json.load(f)
+    for mode in ["f64_plain", "f32_plain", "f64_blocked", "f32_tf32", "f32_3xtf32", "f32_bf16x3"]:
+        if mode == main_mode:
+            continue
+        try:
+            steps = 1 if mode in ("f64_plain", "f32_plain", "f64_blocked") else 3
+            ms, (sg, la) = time_call(lambda: pk.logdet(A, mode), 1, steps, dev)
+            e = {"ms_per_sweep": ms, "tflops": flops(N) / (ms * 1e-3) / 1e12}
+            if g:
+                e["rel_err_vs_oracle"] = abs(float(la) - g["logabs"]) / max(1.0, abs(g["logabs"]))
+                e["sign_match"] = float(sg) == g["sign"]
+            res[mode] = e
+        except Exception as ex:  # report, do not fail the benchmark line
+            res[mode] = {"error": str(ex)[:200]}
+    try:
+        sizes = workloads.batched_sizes(4096, seed=3)
+        mats = workloads.batched_covariances_torch(sizes, seed=3, device=dev)
+        batch = pk.BatchedInputs(mats)
+        ms, _ = time_call(lambda: pk.logdet_batched(batch, "f32_plain"), 2, 5, dev)
+        fl = float(sum(2.0 * int(n) ** 3 / 3.0 for n in sizes))
+        res["batched_4096_f32"] = {"ms": ms, "dets_per_s": 4096 / (ms * 1e-3),
+                                   "tflops": fl / (ms * 1e-3) / 1e12,
+                                   "workload": "4096 SPD X^T X/(2n)+1e-2 I, n uniform on "
+                                               "{32,...,512}, seed 3, FP32, one launch"}
+        del mats, batch
+    except Exception as ex:
+        res["batched_4096_f32"] = {"error": str(ex)[:200]}
+    try:
+        B, n = 256, 1024
+        gen = torch.Generator(device=dev).manual_seed(4)
+        lam = 10.0 ** (-2.0 * torch.rand(B, n, generator=gen, device=dev, dtype=torch.float64))
+        Q, R = torch.linalg.qr(torch.randn(B, n, n, generator=gen, device=dev, dtype=torch.float64))
+        Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
+        X = ((Q * lam[:, None, :]) @ Q.transpose(1, 2)).float()
+        del Q, R
+
+        def fb():
+            Xg = X.detach().requires_grad_(True)
+            out = pk.logabsdet(Xg, "f32_plain")
+            out.sum().backward()
+            return Xg.grad
+        ms, _ = time_call(fb, 1, 2, dev)
+        res["grad_256x1024_f32"] = {"ms_forward_backward": ms,
+                                    "fwd_bwd_tflops": (B * (2 * n ** 3 / 3 + 2 * n ** 3)) /
+                                    (ms * 1e-3) / 1e12}
+    except Exception as ex:
+        res["grad_256x1024_f32"] = {"error": str(ex)[:200]}
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -206,7 +307,19 @@ def run_ours(args):
                "rel_err": abs(float(la) - g["logabs"]) / max(1.0, abs(g["logabs"])),
                "sign_match": float(sg) == g["sign"]}
 
-    kernel, bound, bytes_per_elem = DOMINANT.get(mode, ("update", "hbm", 8))
+    # one fully profiled sweep: per-class shares, then the dominant class
+    _lib.ld_profile_start(None)
+    step()
+    torch.cuda.synchronize(dev)
+    _lib.ld_profile_stop()
+    shares = {}
+    for cls in _lib.ld_profile_classes():
+        nl, tms = _lib.ld_profile_query(cls)
+        shares[cls] = {"launches": nl, "ms": round(tms, 4)}
+    tot = sum(v["ms"] for v in shares.values()) or 1.0
+    for v in shares.values():
+        v["share"] = round(v["ms"] / tot, 4)
+    kernel = max(shares, key=lambda k: shares[k]["ms"]) if shares else "update"
     clocks = ClockSampler(local)
     time.sleep(0.3)
     _lib.ld_profile_start(kernel)
@@ -230,17 +343,10 @@ def run_ours(args):
     ms_max = float(t[0])
     value = world * flops(N) / (ms_max * 1e-3) / 1e12
 
-    # roofline of the dominant kernel: algorithmic bytes over its event time
-    peaks = read_peaks()
-    alg_bytes = bytes_per_elem * (N - 1) * N * (2 * N - 1) / 6.0 * args.steps
-    achieved = alg_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
-    peak = peaks["hbm_gbs"]
-    roofline = {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": None, "peak_source": peaks["source"],
-                "kernel_ms_per_step": k_ms / args.steps,
-                "kernel_launches_per_step": k_launches / args.steps,
-                "algorithmic_bytes_per_step": alg_bytes / args.steps}
+    # roofline of the dominant kernel: algorithmic work over its event time
+    k_bytes, k_flops = _lib.ld_profile_work(kernel)
+    roofline = make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, args.steps)
+    roofline["kernel_shares"] = shares
 
     # end to end: pinned host input -> device -> sweep -> host result, per step
     A_host = torch.from_numpy(A_np).pin_memory()
@@ -266,6 +372,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(A_np, target_s=args.cpu_seconds)
+    paths = None
+    if rank == 0 and not args.no_paths:
+        paths = other_paths(pk, _lib, A, mode, dev, err_gold=gold)
 
     if rank == 0:
         line = {
@@ -278,7 +387,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (N^2 elements > 129 MB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_all, "clocks": clk,
-            "accuracy": err,
+            "accuracy": err, "paths": paths,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -296,6 +405,7 @@ def main():
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paths", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

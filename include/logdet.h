@@ -186,8 +186,8 @@ ld_status ld_profile_classes(char* buf, int64_t cap);
  *          used as TF32, split hi+lo at TF32, or split hi+lo at BF16
  *          (hi*hi + hi*lo + lo*hi)
  *   A, B, D  device, row-major, leading dimensions lda >= K, ldb >= K, ldd >= N;
- *          for the tensor-core modes K must be a multiple of 64, D 16-byte
- *          aligned and ldd a multiple of 4 (else LD_ERR_UNSUPPORTED)
+ *          for the tensor-core modes K must be a multiple of 64 (else
+ *          LD_ERR_UNSUPPORTED)
  * Allocates stream-ordered scratch and waits for `stream` before returning (to
  * report LD_ERR_TIMEOUT from a device wait).
  */

@@ -35,7 +35,7 @@ __device__ __forceinline__ T lu_entry(const T* F, int64_t ldf, int n, int i, int
 }
 
 // Writes the split (or plain) copies of L and U and Y^T = identity for every
-// matrix of the batch. TF32 split: hi = top 19 bits, lo = x - hi.
+// matrix of the batch. TF32 split: hi and lo rounded to nearest TF32.
 template <typename T, bool SPLIT>
 __global__ void unpack_kernel(const void* const* __restrict__ recs, int n, int np, int64_t ldf,
                               T* __restrict__ Lh, T* __restrict__ Ll, T* __restrict__ Uh,
@@ -51,12 +51,13 @@ __global__ void unpack_kernel(const void* const* __restrict__ recs, int n, int n
     const T u = lu_entry(F, ldf, n, i, c, false);
     const T y = (i == c) ? T(1) : T(0);
     if constexpr (SPLIT) {
-      const float lh = __uint_as_float(__float_as_uint((float)l) & 0xffffe000u);
-      const float uh = __uint_as_float(__float_as_uint((float)u) & 0xffffe000u);
+      float lh, ll, uh, ul;
+      tf32_split((float)l, lh, ll);
+      tf32_split((float)u, uh, ul);
       Lh[base + e] = lh;
-      Ll[base + e] = (float)l - lh;
+      Ll[base + e] = ll;
       Uh[base + e] = uh;
-      Ul[base + e] = (float)u - uh;
+      Ul[base + e] = ul;
       Yh[base + e] = y;
       Yl[base + e] = T(0);
     } else {
@@ -125,9 +126,10 @@ __global__ void __launch_bounds__(256)
       const int idx = lane + 32 * q;
       row[idx] = x[q];
       if constexpr (SPLIT) {
-        const float h = __uint_as_float(__float_as_uint((float)x[q]) & 0xffffe000u);
+        float h, lo;
+        tf32_split((float)x[q], h, lo);
         Yh[base + (int64_t)r * np + c0 + idx] = h;
-        Yl[base + (int64_t)r * np + c0 + idx] = (float)x[q] - h;
+        Yl[base + (int64_t)r * np + c0 + idx] = lo;
       }
     }
   }

@@ -14,6 +14,8 @@
 //     to those columns);
 //  3. trailing update A22 -= C R, R = the b factored rows over the remaining
 //     columns (tensor cores for the FP32 modes, FP64 SIMT for LD_F64_BLOCKED).
+#include <stdlib.h>
+
 #include <algorithm>
 
 #include "profile.cuh"
@@ -103,14 +105,21 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);
   const size_t cn_bytes = align_up((size_t)n * b * es, kAlign);
-  const size_t scratch_bytes = 2 * cn_bytes + rankb_scratch_bytes(r.mode, n, n, b) + 2 * kAlign;
+  const size_t panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
+  const size_t scratch_bytes =
+      2 * cn_bytes + panel_bytes + rankb_scratch_bytes(r.mode, n, n, b) + 2 * kAlign;
   void* scratch = nullptr;
   st = scratch_alloc(&scratch, scratch_bytes, stream);
   if (st != LD_OK) return st;
   char* base = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
   T* Cn = reinterpret_cast<T*>(base);
   T* Rt = reinterpret_cast<T*>(base + cn_bytes);
-  void* gemm_scratch = base + 2 * cn_bytes;
+  void* panel_scratch = base + 2 * cn_bytes;
+  void* gemm_scratch = base + 2 * cn_bytes + panel_bytes;
+  // LD_PANEL_PER_PIVOT=1 runs the panel as one launch pair per pivot (the plain
+  // kernels restricted to the panel rows) instead of the persistent panel kernel
+  const char* pp = getenv("LD_PANEL_PER_PIVOT");
+  const bool per_pivot = pp && pp[0] == '1';
   T* F = static_cast<T*>(r.F);
   const size_t trsm_smem = (size_t)b * b * es;
   static bool attr_done[2] = {false, false};
@@ -126,10 +135,17 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   for (int64_t s0 = 0; s0 < n && st == LD_OK; s0 += b) {
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
-    for (int64_t t = 0; t < bb && st == LD_OK; ++t) {
-      const int64_t s = s0 + t;
-      st = launch_pivot_factor<T>(r, s, keep ? 0 : s0, stream);
-      if (st == LD_OK && t + 1 < bb) st = launch_update<T>(r, s, s0 + bb, true, stream);
+    ld_status pst = per_pivot ? LD_ERR_UNSUPPORTED
+                              : launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, stream);
+    if (pst == LD_ERR_UNSUPPORTED) {
+      if (s0 > 0) st = launch_row_argmax<T>(r, s0, m0, stream);
+      for (int64_t t = 0; t < bb && st == LD_OK; ++t) {
+        const int64_t s = s0 + t;
+        st = launch_pivot_factor<T>(r, s, keep ? 0 : s0, stream);
+        if (st == LD_OK && t + 1 < bb) st = launch_update<T>(r, s, s0 + bb, true, stream);
+      }
+    } else {
+      st = pst;
     }
     const int64_t rows = n - s0 - bb;
     if (st != LD_OK || rows <= 0) continue;
@@ -155,7 +171,6 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     }
     st = rankb_update(r.mode, rows, rows, bb, Cn, bb, Rt, bb, F + (s0 + bb) * r.ldf, r.ldf,
                       gemm_scratch, &r.state->flags, stream);
-    if (st == LD_OK) st = launch_row_argmax<T>(r, s0 + bb, rows, stream);
   }
   scratch_free(scratch, stream);
   return st;

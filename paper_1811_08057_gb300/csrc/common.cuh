@@ -135,6 +135,21 @@ struct Vec<float> {
 };
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// x rounded to the nearest TF32 value (ties away from zero), as an FP32 value
+// whose low 13 mantissa bits are zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Split x = hi + lo at TF32 precision with both parts rounded to nearest, so the
+// tensor cores read them exactly and the dropped lo*lo term carries no sign bias.
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - hi);
+}
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 }  // namespace ld

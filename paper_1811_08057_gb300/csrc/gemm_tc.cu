@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128, 1)
     tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), a);
     const int col0 = n0 + c * 32;
     if (clean && row < M) {
-      if (col0 + 32 <= N) {
+      if (col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           float4 v = *reinterpret_cast<float4*>(drow + col0 + 4 * q);
@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(128, 1)
 
 // --------------------------------------------------- operand preparation
 // Splits rows x K (leading dimension ldx) FP32 values into compact hi / lo
-// buffers (rows x K). TF32: hi keeps the sign, exponent and top 10 mantissa bits,
-// lo = x - hi (exact). BF16: hi = bf16(x), lo = bf16(x - hi). Plain TF32 copies.
+// buffers (rows x K). TF32: hi = x rounded to nearest TF32, lo = (x - hi) rounded
+// to nearest TF32. BF16: hi = bf16(x), lo = bf16(x - hi). Plain TF32: x rounded to
+// nearest TF32 (the tensor cores would otherwise drop the low bits).
 template <int KIND, typename Out>
 __global__ void split_kernel(const float* __restrict__ X, int64_t ldx, int rows, int K,
                             Out* __restrict__ hi, Out* __restrict__ lo) {
@@ -188,11 +189,12 @@ __global__ void split_kernel(const float* __restrict__ X, int64_t ldx, int rows,
       hi[idx] = h;
       lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
     } else if constexpr (KIND == kTF32x3) {
-      const float h = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+      float h, l;
+      tf32_split(x, h, l);
       hi[idx] = h;
-      lo[idx] = x - h;
+      lo[idx] = l;
     } else {
-      hi[idx] = x;
+      hi[idx] = tf32_rna(x);
     }
   }
 }
@@ -387,7 +389,6 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
   }
   LD_CHECK_LAUNCH();
   float* Df = static_cast<float*>(D);
-  if ((ldd % 4) != 0 || (reinterpret_cast<uintptr_t>(D) & 15) != 0) return LD_ERR_UNSUPPORTED;
   const TcOperand oa{ah, al, K, 0}, ob{bh, bl, K, 0};
   return rankb_tc(mode, oa, ob, (int)M, (int)N, (int)K, Df, ldd, 0, 1, err, stream);
 }
@@ -398,9 +399,7 @@ ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, 
                    float* D, int64_t ldd, int64_t dstride, int batch, int* err,
                    cudaStream_t stream) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return LD_OK;
-  if (K % 64 != 0 || (ldd % 4) != 0 || (dstride % 4) != 0 ||
-      (reinterpret_cast<uintptr_t>(D) & 15) != 0)
-    return LD_ERR_UNSUPPORTED;
+  if (K % 64 != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0) return LD_ERR_UNSUPPORTED;
   switch (mode) {
     case LD_F32_TF32:
       return launch_tc<kTF32>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);

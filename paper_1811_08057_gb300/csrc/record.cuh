@@ -133,6 +133,15 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
                        const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
                        cudaStream_t stream);
 
+// ---- persistent panel kernel (panel.cu) ----
+size_t panel_scratch_bytes(int G, size_t es);
+// All b pivot steps of the panel at rows [s0, s0+bb) in one cooperative launch;
+// LD_ERR_UNSUPPORTED when its CTAs cannot all be resident (the caller then runs
+// the per-pivot kernels).
+template <typename T>
+ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
+                       void* scratch, cudaStream_t stream);
+
 // ---- blocked path (blocked.cu) ----
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                       bool keep_factors, cudaStream_t stream);

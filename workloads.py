@@ -176,3 +176,29 @@ def batched_covariances_torch(sizes, seed: int = 3, ridge: float = 1e-2, device=
         for k, i in enumerate(idx):
             out[i] = S[k].contiguous()
     return out
+
+
+def spd_reflectors_torch(N: int, seed: int, lo: float, hi: float, device, k: int = 8,
+                         dtype=None):
+    """Q diag(lambda) Q^T with Q a product of k random Householder reflectors
+    (exactly orthogonal, dense), lambda log-uniform in [lo, hi]; FP64 on the GPU in
+    O(k N^2). Stands in for the Haar recipe at sizes where an FP64 QR is too slow
+    on the device. Returns (A, exact_sum_log)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = torch.rand(N, generator=g, device=device, dtype=torch.float64)
+    lam = 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+    A = torch.diag(lam)
+    for _ in range(k):
+        v = torch.randn(N, generator=g, device=device, dtype=torch.float64)
+        v = v / torch.linalg.vector_norm(v)
+        # A <- H A H with H = I - 2 v v^T
+        w = A @ v
+        A = A - 2.0 * torch.outer(v, w) - 2.0 * torch.outer(w, v) + 4.0 * (v @ w) * torch.outer(v, v)
+    A = 0.5 * (A + A.T)
+    sum_log = math.fsum(float(x) for x in torch.log(lam).cpu().tolist())
+    if dtype is not None:
+        A = A.to(dtype)
+    return A, sum_log
