@@ -401,7 +401,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="f64_plain")
+    ap.add_argument("--mode", default="f32_3xtf32")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
