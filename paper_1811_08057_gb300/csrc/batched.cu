@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(kBT)
   int* label = reinterpret_cast<int*>(P + kKB * pw);          // n_max
   int* moved_dst = label + n_max;                             // 2 kKB
   int* moved_src = moved_dst + 2 * kKB;                       // 2 kKB
-  __shared__ Cand red[kBT / 32];
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
   __shared__ int s_swap[kKB];
@@ -133,10 +132,9 @@ __global__ void __launch_bounds__(kBT)
       rec_pivval = reinterpret_cast<double*>(q);
     }
     // stage the matrix into the CTA's workspace (a0)
-    for (int64_t e = tid; e < (int64_t)n * n; e += kBT) {
-      const int i = (int)(e / n), j = (int)(e % n);
-      W[(int64_t)i * ldw + j] = load_in<T>(A, args.a_dtype, (int64_t)i * lda + j);
-    }
+    for (int i = warp; i < n; i += kBT / 32)
+      for (int j = lane; j < n; j += 32)
+        W[(int64_t)i * ldw + j] = load_in<T>(A, args.a_dtype, (int64_t)i * lda + j);
     for (int j = tid; j < n; j += kBT) label[j] = j;
     double sign = 1.0, sum = 0.0, comp = 0.0;  // meaningful in thread 0
     int flags = 0;
@@ -154,37 +152,39 @@ __global__ void __launch_bounds__(kBT)
       __syncthreads();
       for (int t = 0; t < bb; ++t) {
         const int m = m0 - t;
-        // pivot column of panel row t (Sec. 2.2), ties to the smallest label
-        Cand c;
-        cand_init(c);
-        for (int j = tid; j < m; j += kBT) cand_offer(c, (double)P[t * pw + j], label[j], j);
-        cand_block_reduce(c, red);
-        if (tid == 0) {
-          if (c.nan || c.pos < 0 || c.absv == 0.0) {
-            s_bad = c.nan ? kFlagNaN : kFlagSingular;
-          } else {
-            const int l = c.pos;
-            double sg = sign;
-            if (c.v < 0.0) sg = -sg;
-            if (((m + 1) & 1) != 0) sg = -sg;
-            if (l != m - 1) sg = -sg;
-            sign = sg;
-            const double x = log(fabs(c.v));
-            const double tt = sum + x;
-            if (fabs(sum) >= fabs(x))
-              comp += (sum - tt) + x;
-            else
-              comp += (x - tt) + sum;
-            sum = tt;
-            const int lab = label[l];
-            label[l] = label[m - 1];
-            label[m - 1] = lab;
-            s_swap[t] = l;
-            s_l = l;
-            s_p = c.v;
-            if (rec) {
-              rec_pivpos[s0 + t] = l;
-              rec_pivval[s0 + t] = c.v;
+        // pivot column of panel row t (Sec. 2.2), ties to the smallest label: warp 0
+        if (warp == 0) {
+          Cand c;
+          cand_init(c);
+          for (int j = lane; j < m; j += 32) cand_offer(c, (double)P[t * pw + j], label[j], j);
+          cand_warp_reduce(c);
+          if (lane == 0) {
+            if (c.nan || c.pos < 0 || c.absv == 0.0) {
+              s_bad = c.nan ? kFlagNaN : kFlagSingular;
+            } else {
+              const int l = c.pos;
+              double sg = sign;
+              if (c.v < 0.0) sg = -sg;
+              if (((m + 1) & 1) != 0) sg = -sg;
+              if (l != m - 1) sg = -sg;
+              sign = sg;
+              const double x = log(fabs(c.v));
+              const double tt = sum + x;
+              if (fabs(sum) >= fabs(x))
+                comp += (sum - tt) + x;
+              else
+                comp += (x - tt) + sum;
+              sum = tt;
+              const int lab = label[l];
+              label[l] = label[m - 1];
+              label[m - 1] = lab;
+              s_swap[t] = l;
+              s_l = l;
+              s_p = c.v;
+              if (rec) {
+                rec_pivpos[s0 + t] = l;
+                rec_pivval[s0 + t] = c.v;
+              }
             }
           }
         }
@@ -192,17 +192,22 @@ __global__ void __launch_bounds__(kBT)
         if (s_bad) break;
         const int l = s_l;
         const double p = s_p;
-        // exchange column l with the boundary column m-1 in the panel (Sec. 2.4)
+        // row t: factor (Eq. (3), Sec. 2.3) with the exchange of columns l and m-1
+        // applied on the fly (Sec. 2.4); the boundary keeps the pivot. Other panel
+        // rows: the exchange itself.
+        for (int j = tid; j < m - 1; j += kBT) {
+          const T v = (j == l) ? P[t * pw + m - 1] : P[t * pw + j];
+          P[t * pw + j] = (T)((double)v / p);
+          if (j == l) P[t * pw + m - 1] = (T)p;
+        }
         if (l != m - 1) {
           for (int i = tid; i < bb; i += kBT) {
+            if (i == t) continue;
             const T v = P[i * pw + l];
             P[i * pw + l] = P[i * pw + m - 1];
             P[i * pw + m - 1] = v;
           }
         }
-        __syncthreads();
-        // factor row t (Eq. (3), Sec. 2.3); the boundary keeps the pivot
-        for (int j = tid; j < m - 1; j += kBT) P[t * pw + j] = (T)((double)P[t * pw + j] / p);
         __syncthreads();
         // rank-1 update of the remaining panel rows (Eq. (2))
         for (int e = tid; e < (bb - 1 - t) * (m - 1); e += kBT) {
@@ -262,37 +267,64 @@ __global__ void __launch_bounds__(kBT)
           __syncwarp();
         }
       }
-      // trailing rows: one warp per row
-      for (int i = s0 + bb + warp; i < n; i += kBT / 32) {
-        T* row = W + (int64_t)i * ldw;
-        // column exchanges of the panel, composed
-        // (at most 2 * kKB = 32 positions move: one per lane)
-        T mv = T(0);
-        if (lane < nmoved) mv = row[moved_src[lane]];
-        __syncwarp();
-        if (lane < nmoved) row[moved_dst[lane]] = mv;
-        __syncwarp();
-        // multipliers: forward substitution with U[t'][t] = P[t'][m0-1-t]
-        T a = (lane < bb) ? row[m0 - 1 - lane] : T(0);
-        T cm[kKB];
+      // trailing rows: one warp per pair of rows (the panel row values are read once
+      // from shared memory for both)
+      for (int i0 = s0 + bb + 2 * warp; i0 < n; i0 += 2 * (kBT / 32)) {
+        const int nr = min(2, n - i0);
+        T cm[2][kKB];
 #pragma unroll
-        for (int t = 0; t < kKB; ++t) {
-          if (t < bb) {
-            const T ct = __shfl_sync(0xffffffffu, a, t);
-            cm[t] = ct;
-            if (lane > t && lane < bb) a = fma_t(-ct, P[t * pw + (m0 - 1 - lane)], a);
-          } else {
-            cm[t] = T(0);
+        for (int u = 0; u < 2; ++u) {
+          if (u >= nr) {
+#pragma unroll
+            for (int t = 0; t < kKB; ++t) cm[u][t] = T(0);
+            continue;
           }
-        }
-        if (rec && lane < bb) row[m0 - 1 - lane] = a;  // multipliers (L) of this panel
-        // the panel's rank-1 updates, in pivot order, one register per element
-        for (int j = lane; j < ncols; j += 32) {
-          T v = row[j];
+          T* row = W + (int64_t)(i0 + u) * ldw;
+          // column exchanges of the panel, composed (at most 2 * kKB = 32 positions
+          // move: one per lane)
+          T mv = T(0);
+          if (lane < nmoved) mv = row[moved_src[lane]];
+          __syncwarp();
+          if (lane < nmoved) row[moved_dst[lane]] = mv;
+          __syncwarp();
+          // multipliers: forward substitution with U[t'][t] = P[t'][m0-1-t]
+          T a = (lane < bb) ? row[m0 - 1 - lane] : T(0);
 #pragma unroll
-          for (int t = 0; t < kKB; ++t)
-            if (t < bb) v = fma_t(-cm[t], P[t * pw + j], v);
-          row[j] = v;
+          for (int t = 0; t < kKB; ++t) {
+            if (t < bb) {
+              const T ct = __shfl_sync(0xffffffffu, a, t);
+              cm[u][t] = ct;
+              if (lane > t && lane < bb) a = fma_t(-ct, P[t * pw + (m0 - 1 - lane)], a);
+            } else {
+              cm[u][t] = T(0);
+            }
+          }
+          if (rec && lane < bb) row[m0 - 1 - lane] = a;  // multipliers (L) of this panel
+        }
+        // the panel's rank-1 updates, in pivot order, one register per element
+        T* row0 = W + (int64_t)i0 * ldw;
+        T* row1 = row0 + ldw;
+        if (nr == 2) {
+          for (int j = lane; j < ncols; j += 32) {
+            T v0 = row0[j], v1 = row1[j];
+#pragma unroll
+            for (int t = 0; t < kKB; ++t)
+              if (t < bb) {
+                const T r = P[t * pw + j];
+                v0 = fma_t(-cm[0][t], r, v0);
+                v1 = fma_t(-cm[1][t], r, v1);
+              }
+            row0[j] = v0;
+            row1[j] = v1;
+          }
+        } else {
+          for (int j = lane; j < ncols; j += 32) {
+            T v = row0[j];
+#pragma unroll
+            for (int t = 0; t < kKB; ++t)
+              if (t < bb) v = fma_t(-cm[0][t], P[t * pw + j], v);
+            row0[j] = v;
+          }
         }
       }
       __syncthreads();
