@@ -6,12 +6,33 @@
 
 namespace ld {
 
+// Keeps freed workspace in the device's default memory pool instead of returning
+// it to the driver at every synchronisation (the pool's default), so repeated
+// calls reuse their workspace without re-mapping it. Once per device.
+static void keep_pool_memory() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 // Stream-ordered scratch allocation. LD_FAULT_INJECT_ALLOC=1 in the environment
 // makes it fail, so the error path can be exercised without exhausting memory.
 ld_status scratch_alloc(void** p, size_t bytes, cudaStream_t stream) {
   *p = nullptr;
   const char* inj = getenv("LD_FAULT_INJECT_ALLOC");
   if (inj && inj[0] == '1') return LD_ERR_ALLOC;
+  keep_pool_memory();
   if (bytes == 0) bytes = kAlign;
   cudaError_t e = cudaMallocAsync(p, bytes, stream);
   if (e != cudaSuccess) {

@@ -32,7 +32,7 @@ constexpr int kPanel = 128;  // b, a multiple of 64 (tensor-core K-chunks)
 template <typename T, int KMAX>
 __global__ void __launch_bounds__(256)
     trsm_kernel(T* __restrict__ F, int64_t ldf, int n, int s0, int bb, int m0, int row_begin,
-                T* __restrict__ Cn) {
+                T* __restrict__ Cn, const int* __restrict__ moves) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // bb x bb, U[t' * bb + t]
   for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
@@ -45,6 +45,23 @@ __global__ void __launch_bounds__(256)
   for (int i = row_begin + blockIdx.x * warps + (threadIdx.x >> 5); i < n;
        i += gridDim.x * warps) {
     T* row = F + (int64_t)i * ldf;
+    if (moves) {
+      // the panel's column exchanges, composed (moves[0] pairs of (dst, src))
+      const int nm = moves[0];
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        v[q] = (k < nm) ? row[moves[2 + 2 * k]] : T(0);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        if (k < nm) row[moves[1 + 2 * k]] = v[q];
+      }
+      __syncwarp();
+    }
     T a[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
@@ -105,7 +122,8 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);
   const size_t cn_bytes = align_up((size_t)n * b * es, kAlign);
-  const size_t panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
+  const size_t panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign) +
+                             align_up(panel_cluster_scratch_bytes(), kAlign);
   const size_t scratch_bytes =
       2 * cn_bytes + panel_bytes + rankb_scratch_bytes(r.mode, n, n, b) + 2 * kAlign;
   void* scratch = nullptr;
@@ -115,6 +133,13 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   T* Cn = reinterpret_cast<T*>(base);
   T* Rt = reinterpret_cast<T*>(base + cn_bytes);
   void* panel_scratch = base + 2 * cn_bytes;
+  void* cluster_scratch =
+      base + 2 * cn_bytes + align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
+  const int* cluster_moves = reinterpret_cast<const int*>(
+      static_cast<char*>(cluster_scratch) + align_up((size_t)128 * 16 * 4, kAlign));
+  // LD_PANEL=grid selects the grid-wide panel kernel instead of the cluster one
+  const char* pk = getenv("LD_PANEL");
+  const bool no_cluster = pk && pk[0] == 'g';
   void* gemm_scratch = base + 2 * cn_bytes + panel_bytes;
   // LD_PANEL_PER_PIVOT=1 runs the panel as one launch pair per pivot (the plain
   // kernels restricted to the panel rows) instead of the persistent panel kernel
@@ -135,8 +160,14 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   for (int64_t s0 = 0; s0 < n && st == LD_OK; s0 += b) {
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
-    ld_status pst = per_pivot ? LD_ERR_UNSUPPORTED
-                              : launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, stream);
+    bool used_cluster = false;
+    ld_status pst = LD_ERR_UNSUPPORTED;
+    if (!per_pivot && !no_cluster && sizeof(T) == 4) {
+      pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cluster_scratch, stream);
+      used_cluster = (pst == LD_OK);
+    }
+    if (!per_pivot && pst == LD_ERR_UNSUPPORTED)
+      pst = launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, stream);
     if (pst == LD_ERR_UNSUPPORTED) {
       if (s0 > 0) st = launch_row_argmax<T>(r, s0, m0, stream);
       for (int64_t t = 0; t < bb && st == LD_OK; ++t) {
@@ -154,7 +185,8 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
       const int grid = (int)std::min<int64_t>(ceil_div(rows, warps), device_sm_count() * 2);
       ProfScope ps("trsm", stream, 3.0 * es * (double)rows * bb, (double)rows * bb * bb);
       trsm_kernel<T, kPanel / 32><<<grid, 256, trsm_smem, stream>>>(
-          F, r.ldf, (int)n, (int)s0, (int)bb, (int)m0, (int)(s0 + bb), Cn);
+          F, r.ldf, (int)n, (int)s0, (int)bb, (int)m0, (int)(s0 + bb), Cn,
+          used_cluster ? cluster_moves : nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) {
       st = LD_ERR_CUDA;

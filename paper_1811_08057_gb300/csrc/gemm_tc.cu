@@ -37,6 +37,10 @@ struct TcCfg {
   static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
   static constexpr int NSUB = BK / KSTEP;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  // K-chunks rotate over NACC accumulators in TMEM (NACC x BN columns), summed in
+  // FP32 in the epilogue: each tensor-core accumulation chain is NACC times shorter.
+  static constexpr int NACC = 4;
+  static constexpr int TMEM_COLS = NACC * BN;  // 512: the whole TMEM of the SM
 };
 
 template <int KIND>
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(128, 1)
     tc::tma_prefetch_desc(&mBh);
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, C::BN);
+    tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -97,8 +101,7 @@ __global__ void __launch_bounds__(128, 1)
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    uint32_t acc = 0;
+    // MMA issuer: K-chunk kc accumulates into accumulator kc % NACC
     for (int kc = 0; kc < nk; ++kc) {
       const int s = kc % C::STAGES, r = kc / C::STAGES;
       if (!tc::mbar_wait(&full[s], r & 1, err)) break;
@@ -106,19 +109,21 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
       const uint32_t ah = st, al = st + C::A_BYTES;
       const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
+      const uint32_t d = tmem + (uint32_t)((kc % C::NACC) * C::BN);
+      uint32_t acc = (kc >= C::NACC) ? 1u : 0u;  // first chunk of an accumulator overwrites
 #pragma unroll
       for (int k = 0; k < C::NSUB; ++k) {
         const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
         if (KIND == kTF32) {
-          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
         } else if (KIND == kTF32x3) {
-          tc::mma_tf32(tmem, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_tf32(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
         } else {
-          tc::mma_f16(tmem, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_f16(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_f16(tmem, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
         }
         acc = 1u;
       }
@@ -135,10 +140,18 @@ __global__ void __launch_bounds__(128, 1)
   const bool clean = got && (*reinterpret_cast<volatile int*>(err) == 0);
   const int row = m0 + warp * 32 + lane;
   float* drow = D + (int64_t)row * ldd;
+  const int nacc = nk < C::NACC ? nk : C::NACC;
 #pragma unroll 1
   for (int c = 0; c < C::BN / 32; ++c) {
     float a[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), a);
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
+    tc::tmem_ld32(lane_base, a);
+    for (int q = 1; q < nacc; ++q) {  // sum the accumulators in FP32 (round to nearest)
+      float b[32];
+      tc::tmem_ld32(lane_base + (uint32_t)(q * C::BN), b);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) a[i] += b[i];
+    }
     const int col0 = n0 + c * 32;
     if (clean && row < M) {
       if (col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0) {
@@ -168,7 +181,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, C::BN);
+  if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
 // --------------------------------------------------- operand preparation
