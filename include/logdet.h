@@ -197,6 +197,27 @@ ld_status ld_rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const v
                           int64_t lda, const void* B, int64_t ldb, void* D, int64_t ldd,
                           void* stream);
 
+/*
+ * ld_logdet_noalloc - ld_logdet with mode LD_F64_PLAIN for callers that cannot
+ * allocate device memory when they need the result (for example inside a stream
+ * capture that forbids new allocations, or under a fixed device-memory budget
+ * reserved up front). The paper has no counterpart: this is a deployment variant
+ * of the same sweep. It allocates nothing: its workspace is a fixed array of
+ * about 8 MiB in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *   A, a_dtype, n, lda, stream, sign, logabs  as ld_logdet (outputs may be host
+ *            or device pointers; host pointers make the call wait for `stream`)
+ *   n        at most 1024; larger n returns LD_ERR_UNSUPPORTED without device work
+ * The first call on each device looks up the workspace's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. All
+ * calls share the one workspace, which keeps the last call's contents (every
+ * value a call reads is written by that call first). Calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race on it: order
+ * them on one stream or synchronise between them.
+ */
+ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, void* stream,
+                            double* sign, double* logabs);
+
 /* Human-readable name of a status code (static storage). */
 const char* ld_status_string(ld_status s);
 

@@ -53,6 +53,7 @@ SIGNATURES = {
                                  _int),
     "ld_logdet_backward_batched": ([_vp, _i64, _i64, _int, _vp, _vp, _i64, _vp], _int),
     "ld_rankb_update": ([_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _int),
+    "ld_logdet_noalloc": ([_vp, _int, _i64, _i64, _vp, _pd, _pd], _int),
     "ld_profile_start": ([ctypes.c_char_p], _int),
     "ld_profile_stop": ([], _int),
     "ld_profile_query": ([ctypes.c_char_p, _vp, _vp], _int),
@@ -140,6 +141,10 @@ def ld_logdet_backward_batched(factors, count, n, mode, g, grads, ldg, stream) -
 
 def ld_rankb_update(mode, M, N, K, A, lda, B, ldb, D, ldd, stream) -> int:
     return load().ld_rankb_update(mode, M, N, K, A, lda, B, ldb, D, ldd, stream)
+
+
+def ld_logdet_noalloc(A, a_dtype, n, lda, stream, sign, logabs) -> int:
+    return load().ld_logdet_noalloc(A, a_dtype, n, lda, stream, sign, logabs)
 
 
 def ld_profile_start(kernel=None) -> int:
