@@ -218,6 +218,17 @@ ld_status ld_rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const v
 ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, void* stream,
                             double* sign, double* logabs);
 
+/*
+ * Tuning table used by the launchers (process-wide; the autotuner in the Python
+ * package sets it from timings, see paper_1811_08057_gb300/tune.py):
+ *   "blocked_b"       panel width b of the blocked sweep: 64 or 128 (default 128)
+ *   "batched_kb_<k>"  panels of the batched sweep for matrices with n in
+ *                     [64k, 64k+63] (k = 0..8; k = 8 also covers larger n): 8 or 16
+ * LD_ERR_INVALID_ARG for an unknown name or value.
+ */
+ld_status ld_set_tuning(const char* name, int64_t value);
+ld_status ld_get_tuning(const char* name, int64_t* value);
+
 /* Human-readable name of a status code (static storage). */
 const char* ld_status_string(ld_status s);
 

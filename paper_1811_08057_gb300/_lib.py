@@ -59,6 +59,8 @@ SIGNATURES = {
     "ld_profile_query": ([ctypes.c_char_p, _vp, _vp], _int),
     "ld_profile_work": ([ctypes.c_char_p, _vp, _vp], _int),
     "ld_profile_classes": ([_vp, _i64], _int),
+    "ld_set_tuning": ([ctypes.c_char_p, _i64], _int),
+    "ld_get_tuning": ([ctypes.c_char_p, _vp], _int),
     "ld_status_string": ([_int], ctypes.c_char_p),
     "ld_version": ([], ctypes.c_char_p),
 }
@@ -180,6 +182,16 @@ def ld_profile_classes():
     check("ld_profile_classes", load().ld_profile_classes(ctypes.addressof(buf), 4096))
     v = buf.value.decode()
     return [x for x in v.split(",") if x]
+
+
+def ld_set_tuning(name: str, value: int) -> int:
+    return load().ld_set_tuning(name.encode(), int(value))
+
+
+def ld_get_tuning(name: str) -> int:
+    v = ctypes.c_int64()
+    check("ld_get_tuning", load().ld_get_tuning(name.encode(), ctypes.addressof(v)))
+    return v.value
 
 
 def ld_status_string(code) -> str:

@@ -58,6 +58,15 @@ bool is_device_pointer(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ---- tuning table (process-wide; set by ld_set_tuning, read by the launchers) ----
+namespace {
+int g_blocked_b = 128;              // panel width of the blocked sweep (64 or 128)
+int g_batched_kb[kTuneBuckets] = {16, 16, 16, 16, 16, 16, 16, 16, 16};
+}  // namespace
+
+int tuned_blocked_b() { return g_blocked_b; }
+const int* tuned_batched_kb() { return g_batched_kb; }
+
 static ld_status run_sweep(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                            bool keep, cudaStream_t stream) {
   switch (r.mode) {
@@ -153,5 +162,36 @@ const char* ld_status_string(ld_status s) {
 }
 
 const char* ld_version(void) { return "liblogdet 0.1 sm_103a"; }
+
+ld_status ld_set_tuning(const char* name, int64_t value) {
+  if (!name) return LD_ERR_INVALID_ARG;
+  if (strcmp(name, "blocked_b") == 0) {
+    if (value != 64 && value != 128) return LD_ERR_INVALID_ARG;
+    ld::g_blocked_b = (int)value;
+    return LD_OK;
+  }
+  if (strncmp(name, "batched_kb_", 11) == 0) {
+    const int k = atoi(name + 11);
+    if (k < 0 || k >= ld::kTuneBuckets || (value != 8 && value != 16)) return LD_ERR_INVALID_ARG;
+    ld::g_batched_kb[k] = (int)value;
+    return LD_OK;
+  }
+  return LD_ERR_INVALID_ARG;
+}
+
+ld_status ld_get_tuning(const char* name, int64_t* value) {
+  if (!name || !value) return LD_ERR_INVALID_ARG;
+  if (strcmp(name, "blocked_b") == 0) {
+    *value = ld::g_blocked_b;
+    return LD_OK;
+  }
+  if (strncmp(name, "batched_kb_", 11) == 0) {
+    const int k = atoi(name + 11);
+    if (k < 0 || k >= ld::kTuneBuckets) return LD_ERR_INVALID_ARG;
+    *value = ld::g_batched_kb[k];
+    return LD_OK;
+  }
+  return LD_ERR_INVALID_ARG;
+}
 
 }  // extern "C"

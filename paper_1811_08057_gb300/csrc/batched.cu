@@ -40,6 +40,7 @@ struct BatchedArgs {
   double* logabs;
   void* const* factors;  // optional: one factor record per matrix (else nullptr)
   int mode;
+  int kb_table[kTuneBuckets];  // panel depth per size class (<= kKB)
 };
 
 // Counting sort of the matrix indices by decreasing size (one CTA).
@@ -136,13 +137,14 @@ __global__ void __launch_bounds__(kBT)
       for (int j = lane; j < n; j += 32)
         W[(int64_t)i * ldw + j] = load_in<T>(A, args.a_dtype, (int64_t)i * lda + j);
     for (int j = tid; j < n; j += kBT) label[j] = j;
+    const int kbm = args.kb_table[min(n / 64, kTuneBuckets - 1)];  // this matrix's panel depth
     double sign = 1.0, sum = 0.0, comp = 0.0;  // meaningful in thread 0
     int flags = 0;
     if (tid == 0) s_bad = 0;
     __syncthreads();
 
-    for (int s0 = 0; s0 < n; s0 += kKB) {
-      const int bb = min(kKB, n - s0);
+    for (int s0 = 0; s0 < n; s0 += kbm) {
+      const int bb = min(kbm, n - s0);
       const int m0 = n - s0;
       // panel rows into shared memory
       for (int e = tid; e < bb * m0; e += kBT) {
@@ -401,7 +403,9 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   if (st == LD_OK) {
     BatchedArgs a{A_ptrs, n,      lda,    (int)a_dtype, (int)count, (int)n_max, ldw,
-                  order,  counter, signs, logabs,       factors,    (int)mode};
+                  order,  counter, signs, logabs,       factors,    (int)mode, {}};
+    const int* kbt = tuned_batched_kb();
+    for (int k = 0; k < kTuneBuckets; ++k) a.kb_table[k] = std::min(kKB, std::max(1, kbt[k]));
     ProfScope ps("batched", stream);
     batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, factors ? nullptr : ws);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;

@@ -117,7 +117,7 @@ template <typename T>
 ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r, bool keep,
                         cudaStream_t stream) {
   const int64_t n = r.n;
-  const int b = kPanel;
+  const int b = std::min(kPanel, tuned_blocked_b());
   ld_status st = launch_stage<T>(A, a_dtype, lda, r, stream);
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);

@@ -85,6 +85,12 @@ inline size_t record_layout(int64_t n, ld_mode mode, void* base, Record* r) {
 
 int device_sm_count();
 
+// Tuning table (ld_set_tuning): blocked panel width, batched panel depth per
+// size class (class k holds n in [64k, 64k + 63]; the last class all larger n).
+constexpr int kTuneBuckets = 9;
+int tuned_blocked_b();
+const int* tuned_batched_kb();
+
 // ---- plain-path launchers (plain.cu) ----
 // Copies A into F (converting to the storage type), sets colperm = identity,
 // resets the sweep state and writes the pivot candidates of row 0.

@@ -53,3 +53,17 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert _lib.ld_logdet(0x1000, 0, 8, 8, 9, None, ps, pl) == INVALID
     assert _lib.ld_logdet(0x1000, 7, 8, 8, 0, None, ps, pl) == INVALID
     assert _lib.ld_logdet_factor(0x1000, 0, 8, 8, 0, None, None, ps, pl) == INVALID
+
+
+def test_tuning_table_round_trip(lib):
+    assert _lib.ld_get_tuning("blocked_b") in (64, 128)
+    assert _lib.ld_set_tuning("blocked_b", 64) == 0
+    assert _lib.ld_get_tuning("blocked_b") == 64
+    assert _lib.ld_set_tuning("blocked_b", 100) == 1  # not a supported width
+    assert _lib.ld_set_tuning("blocked_b", 128) == 0
+    for k in range(9):
+        assert _lib.ld_set_tuning(f"batched_kb_{k}", 8) == 0
+        assert _lib.ld_get_tuning(f"batched_kb_{k}") == 8
+        assert _lib.ld_set_tuning(f"batched_kb_{k}", 16) == 0
+    assert _lib.ld_set_tuning("batched_kb_9", 8) == 1
+    assert _lib.ld_set_tuning("nonsense", 1) == 1
