@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kBT)
         // rows: the exchange itself.
         for (int j = tid; j < m - 1; j += kBT) {
           const T v = (j == l) ? P[t * pw + m - 1] : P[t * pw + j];
-          P[t * pw + j] = (T)((double)v / p);
+          P[t * pw + j] = (sizeof(T) == 4) ? (T)__fdiv_rn((float)v, (float)p) : (T)((double)v / p);
           if (j == l) P[t * pw + m - 1] = (T)p;
         }
         if (l != m - 1) {

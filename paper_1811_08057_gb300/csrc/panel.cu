@@ -533,18 +533,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
     const int l = s_l;
     const float pf = s_p;
     const double p = (double)pf;
-    if (c == 0 && tid == 0) {
-      // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1 (Sec. 2.4)
-      if (p < 0.0) sign = -sign;
-      if (((m + 1) & 1) != 0) sign = -sign;
-      if (l != m - 1) sign = -sign;
-      const double x = log(fabs(p));
-      const double tt = sum + x;
-      if (fabs(sum) >= fabs(x))
-        comp += (sum - tt) + x;
-      else
-        comp += (x - tt) + sum;
-      sum = tt;
+    if (c == 0 && tid == 0) {  // the sign and the log-sum are accumulated after the panel
       a.pivpos[a.s0 + t] = l;
       a.pivval[a.s0 + t] = p;
     }
@@ -567,7 +556,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
     for (int j = j_lo + tid; j < jend; j += kPT) {
       const int jj = j - j_lo;
       const float v = (j == l) ? lcol[t] : S[t * W + jj];
-      S[t * W + jj] = (float)((double)v / p);
+      S[t * W + jj] = __fdiv_rn(v, pf);  // IEEE FP32 divide = FP64 quotient rounded
     }
     __syncthreads();  // B3
     // rank-1 update of rows t+1.. and the pivot search of row t+1
@@ -590,6 +579,23 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
   }
   for (int j = tid; j < w_own; j += kPT) a.colperm[j_lo + j] = lab[j];
   if (c == 0 && tid == 0 && !bad) {
+    // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1 (Sec. 2.4),
+    // log|p| in pivot order (same Neumaier steps as per pivot)
+    for (int t = 0; t < bb; ++t) {
+      const int m = m0 - t;
+      const double pv = a.pivval[a.s0 + t];
+      const int l = a.pivpos[a.s0 + t];
+      if (pv < 0.0) sign = -sign;
+      if (((m + 1) & 1) != 0) sign = -sign;
+      if (l != m - 1) sign = -sign;
+      const double x = log(fabs(pv));
+      const double tt = sum + x;
+      if (fabs(sum) >= fabs(x))
+        comp += (sum - tt) + x;
+      else
+        comp += (x - tt) + sum;
+      sum = tt;
+    }
     a.st->sign = sign;
     a.st->sum = sum;
     a.st->comp = comp;

@@ -186,20 +186,10 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         break;
       }
       const int l = s_l;
-      const double p = (double)s_p;
+      const float pf = s_p;
+      const double p = (double)pf;
       if (tid == 0) s_swap[t] = l;
-      if (c == 0 && tid == 0) {
-        // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1 (Sec. 2.4)
-        if (p < 0.0) sign = -sign;
-        if (((m + 1) & 1) != 0) sign = -sign;
-        if (l != m - 1) sign = -sign;
-        const double x = log(fabs(p));
-        const double tt = sum + x;
-        if (fabs(sum) >= fabs(x))
-          comp += (sum - tt) + x;
-        else
-          comp += (x - tt) + sum;
-        sum = tt;
+      if (c == 0 && tid == 0) {  // the sign and the log-sum are accumulated after the panel
         a.pivpos[a.s0 + q0 + t] = l;
         a.pivval[a.s0 + q0 + t] = p;
       }
@@ -219,7 +209,8 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       for (int j = j_lo + tid; j < jend; j += kCT) {
         const int jj = j - j_lo;
         const float v = (j == l) ? lcol[t] : S[t * W + jj];
-        S[t * W + jj] = (float)((double)v / p);
+        // IEEE FP32 divide: equal to the FP64 quotient rounded to FP32
+        S[t * W + jj] = __fdiv_rn(v, pf);
       }
       __syncthreads();
       const int nj = max(0, jend - j_lo);
@@ -346,6 +337,23 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         }
       a.moves[0] = bad ? 0 : k2;
       if (!bad) {
+        // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
+        // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
+        for (int t = 0; t < bb; ++t) {
+          const int m = m0 - t;
+          const double pv = a.pivval[a.s0 + t];
+          const int l = a.pivpos[a.s0 + t];
+          if (pv < 0.0) sign = -sign;
+          if (((m + 1) & 1) != 0) sign = -sign;
+          if (l != m - 1) sign = -sign;
+          const double x = log(fabs(pv));
+          const double tt = sum + x;
+          if (fabs(sum) >= fabs(x))
+            comp += (sum - tt) + x;
+          else
+            comp += (x - tt) + sum;
+          sum = tt;
+        }
         a.st->sign = sign;
         a.st->sum = sum;
         a.st->comp = comp;

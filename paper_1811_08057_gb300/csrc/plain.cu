@@ -31,6 +31,11 @@ __device__ __forceinline__ T to_t(double x) {
   return static_cast<T>(x);
 }
 
+// r = a / p in the storage type: FP64 IEEE divide for FP64 storage; for FP32 the
+// IEEE FP32 divide, which equals the FP64 quotient rounded to FP32 (53 >= 2*24+2).
+__device__ __forceinline__ double div_t(double a, double p) { return a / p; }
+__device__ __forceinline__ float div_t(float a, double p) { return __fdiv_rn(a, (float)p); }
+
 // ---------------------------------------------------------------- stage (a0)
 template <typename T, typename In>
 __global__ void __launch_bounds__(kThreads)
@@ -123,12 +128,11 @@ __global__ void __launch_bounds__(kThreads)
       if (l == m - 1) {
         prow[m - 1] = to_t<T>(p);
       } else {
-        const double e = (double)prow[m - 1];
-        prow[l] = to_t<T>(e / p);
+        prow[l] = div_t(prow[m - 1], p);
         prow[m - 1] = to_t<T>(p);
       }
     } else if (t != m - 1) {
-      prow[t] = to_t<T>((double)prow[t] / p);
+      prow[t] = div_t(prow[t], p);
     }
   }
   const int i = swap_row_begin + t;

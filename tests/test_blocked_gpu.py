@@ -57,7 +57,7 @@ def test_blocked_gaussian_tolerance(mode, n):
         assert math.isfinite(float(l))
         return
     assert float(s) == ref.sign
-    assert err <= TOL_GAUSSIAN_SMALL[mode], (mode, n, float(l), ref.logabs)
+    assert err <= TOL[mode], (mode, n, float(l), ref.logabs)
 
 
 @pytest.mark.parametrize("mode", sorted(TOL))
