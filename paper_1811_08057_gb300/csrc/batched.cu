@@ -155,11 +155,24 @@ __global__ void __launch_bounds__(kBT)
       for (int t = 0; t < bb; ++t) {
         const int m = m0 - t;
         // pivot column of panel row t (Sec. 2.2), ties to the smallest label: warp 0
+        // (FP32 storage compares in FP32: exact, and off the FP64 pipe)
         if (warp == 0) {
           Cand c;
-          cand_init(c);
-          for (int j = lane; j < m; j += 32) cand_offer(c, (double)P[t * pw + j], label[j], j);
-          cand_warp_reduce(c);
+          if constexpr (sizeof(T) == 4) {
+            CandF cf;
+            candf_init(cf);
+            for (int j = lane; j < m; j += 32) candf_offer(cf, (float)P[t * pw + j], label[j], j);
+            candf_warp_reduce(cf);
+            c.absv = cf.absv;
+            c.v = cf.v;
+            c.label = cf.label;
+            c.pos = cf.pos;
+            c.nan = cf.nan;
+          } else {
+            cand_init(c);
+            for (int j = lane; j < m; j += 32) cand_offer(c, (double)P[t * pw + j], label[j], j);
+            cand_warp_reduce(c);
+          }
           if (lane == 0) {
             if (c.nan || c.pos < 0 || c.absv == 0.0) {
               s_bad = c.nan ? kFlagNaN : kFlagSingular;
@@ -211,10 +224,10 @@ __global__ void __launch_bounds__(kBT)
           }
         }
         __syncthreads();
-        // rank-1 update of the remaining panel rows (Eq. (2))
-        for (int e = tid; e < (bb - 1 - t) * (m - 1); e += kBT) {
-          const int i = t + 1 + e / (m - 1), j = e % (m - 1);
-          P[i * pw + j] = fma_t(-P[i * pw + m - 1], P[t * pw + j], P[i * pw + j]);
+        // rank-1 update of the remaining panel rows (Eq. (2)), one warp per row
+        for (int i = t + 1 + warp; i < bb; i += kBT / 32) {
+          const T ci = P[i * pw + m - 1];
+          for (int j = lane; j < m - 1; j += 32) P[i * pw + j] = fma_t(-ci, P[t * pw + j], P[i * pw + j]);
         }
         __syncthreads();
       }

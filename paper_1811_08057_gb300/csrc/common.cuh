@@ -110,6 +110,99 @@ __device__ __forceinline__ void cand_block_reduce(Cand& c, Cand* scratch) {
   __syncthreads();
 }
 
+// FP32 candidate for FP32 storage (the same ordering as Cand, compared in FP32:
+// exact, and without the FP64 pipe).
+struct CandF {
+  float absv;  // -1 for "no candidate"
+  float v;
+  int label;
+  int pos;
+  int nan;
+};
+
+__device__ __forceinline__ void candf_init(CandF& c) {
+  c.absv = -1.f;
+  c.v = 0.f;
+  c.label = 0x7fffffff;
+  c.pos = -1;
+  c.nan = 0;
+}
+
+__device__ __forceinline__ bool candf_better(float absv, int label, const CandF& b) {
+  return absv > b.absv || (absv == b.absv && label < b.label);
+}
+
+__device__ __forceinline__ void candf_offer(CandF& c, float v, int label, int pos) {
+  const float a = fabsf(v);
+  if (a != a) {
+    c.nan = 1;
+    return;
+  }
+  if (candf_better(a, label, c)) {
+    c.absv = a;
+    c.v = v;
+    c.label = label;
+    c.pos = pos;
+  }
+}
+
+// Merges o into c; returns true if o's candidate won.
+__device__ __forceinline__ bool candf_merge(CandF& c, const CandF& o) {
+  c.nan |= o.nan;
+  if (o.pos >= 0 && candf_better(o.absv, o.label, c)) {
+    c.absv = o.absv;
+    c.v = o.v;
+    c.label = o.label;
+    c.pos = o.pos;
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void candf_warp_reduce(CandF& c) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    CandF o;
+    o.absv = __shfl_xor_sync(0xffffffffu, c.absv, off);
+    o.v = __shfl_xor_sync(0xffffffffu, c.v, off);
+    o.label = __shfl_xor_sync(0xffffffffu, c.label, off);
+    o.pos = __shfl_xor_sync(0xffffffffu, c.pos, off);
+    o.nan = __shfl_xor_sync(0xffffffffu, c.nan, off);
+    candf_merge(c, o);
+  }
+}
+
+// Sign and Neumaier log-sum of pivots [first, first + count) of a panel whose
+// first step has `m0` active columns, in pivot order: warp-parallel logs, one
+// lane adds them in order (the same operations as a per-pivot accumulation).
+__device__ __forceinline__ void panel_sign_logsum(const double* pivval, const int* pivpos,
+                                                  int first, int count, int m0, double& sign,
+                                                  double& sum, double& comp) {
+  const int lane = threadIdx.x & 31;
+  for (int t0 = 0; t0 < count; t0 += 32) {
+    const int t = t0 + lane;
+    const double x = (t < count) ? log(fabs(pivval[first + t])) : 0.0;
+    for (int k = 0; k < 32 && t0 + k < count; ++k) {
+      const double xk = __shfl_sync(0xffffffffu, x, k);
+      if (lane == 0) {
+        const int tt = t0 + k;
+        const int m = m0 - tt;
+        const double pv = pivval[first + tt];
+        const int l = pivpos[first + tt];
+        if (pv < 0.0) sign = -sign;
+        if (((m + 1) & 1) != 0) sign = -sign;
+        if (l != m - 1) sign = -sign;
+        const double s2 = sum + xk;
+        if (fabs(sum) >= fabs(xk))
+          comp += (sum - s2) + xk;
+        else
+          comp += (xk - s2) + sum;
+        sum = s2;
+      }
+    }
+  }
+}
+
 // Neumaier step on the state's compensated sum.
 __device__ __forceinline__ void state_add_log(SweepState* st, double x) {
   double s = st->sum;

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
   float* pcol = S + (size_t)bb * W;               // kPanelMax: the pivot column
   float* lcol = pcol + kPanelMax;                 // kPanelMax: the boundary column
   int* lab = reinterpret_cast<int*>(lcol + kPanelMax);  // W labels
-  __shared__ Cand wred[kPT / 32];
+  __shared__ CandF wred[kPT / 32];
   __shared__ int s_l, s_ok, s_lab, s_lastlab;
   __shared__ float s_p;
   float* F = a.F;
@@ -386,24 +386,24 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
   int pend_l = -1, pend_m = -1;
 
   // candidate of row 0 (later rows: fused into the update)
-  Cand cd;
-  cand_init(cd);
+  CandF cd;
+  candf_init(cd);
   for (int j = tid; j < w_own; j += kPT)
-    if (j_lo + j < m0) cand_offer(cd, (double)S[j], lab[j], j_lo + j);
+    if (j_lo + j < m0) candf_offer(cd, S[j], lab[j], j_lo + j);
 
   for (int t = 0; t < bb && !bad; ++t) {
     const int m = m0 - t;
     const int par = t & 1;
-    cand_warp_reduce(cd);
+    candf_warp_reduce(cd);
     if (lane == 0) wred[warp] = cd;
     __syncthreads();  // B1: per-warp candidates of row t in shared memory
     if (warp == 0) {
-      Cand b;
+      CandF b;
       if (lane < kPT / 32)
         b = wred[lane];
       else
-        cand_init(b);
-      cand_warp_reduce(b);
+        candf_init(b);
+      candf_warp_reduce(b);
       // publish: candidate column (+ its position), boundary column (+ label), slot
       float* mycol = a.cols + ((size_t)par * G + c) * CP;
       if (b.pos >= 0) {
@@ -416,8 +416,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
         for (int i = lane; i < bb; i += 32) lc[i] = S[i * W + (m - 1 - j_lo)];
         if (lane == 0) lc[kPanelMax] = __int_as_float(lab[m - 1 - j_lo]);
       }
-      __threadfence();
-      __syncwarp();
+      __syncwarp();  // the release below is cumulative over the warp's stores
       if (lane == 0) {
         uint32_t vbits, lbl;
         if (b.nan) {
@@ -427,7 +426,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
           vbits = 0;
           lbl = kNoCand;
         } else {
-          vbits = __float_as_uint((float)b.v);
+          vbits = __float_as_uint(b.v);
           lbl = (uint32_t)b.label;
         }
         const unsigned long long word = (unsigned long long)vbits |
@@ -459,8 +458,8 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
         }
       }
       timed_out = __any_sync(0xffffffffu, timed_out);
-      Cand best;
-      cand_init(best);
+      CandF best;
+      candf_init(best);
       int wbest = -1;
 #pragma unroll
       for (int q = 0; q < SL; ++q) {
@@ -471,10 +470,10 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
           best.nan = 1;
           continue;
         }
-        const double av = fabs((double)v);
-        if (cand_better(av, (int)lbl, best)) {
+        const float av = fabsf(v);
+        if (candf_better(av, (int)lbl, best)) {
           best.absv = av;
-          best.v = (double)v;
+          best.v = v;
           best.label = (int)lbl;
           best.pos = 0;
           wbest = lane + 32 * q;
@@ -482,21 +481,19 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        Cand o;
+        CandF o;
         o.absv = __shfl_xor_sync(0xffffffffu, best.absv, off);
         o.v = __shfl_xor_sync(0xffffffffu, best.v, off);
         o.label = __shfl_xor_sync(0xffffffffu, best.label, off);
         o.pos = __shfl_xor_sync(0xffffffffu, best.pos, off);
         o.nan = __shfl_xor_sync(0xffffffffu, best.nan, off);
         const int ow = __shfl_xor_sync(0xffffffffu, wbest, off);
-        const bool better = o.pos >= 0 && cand_better(o.absv, o.label, best);
-        cand_merge(best, o);
-        if (better) wbest = ow;
+        if (candf_merge(best, o)) wbest = ow;
       }
       int ok = 1;
       if (timed_out) ok = 0;
       else if (best.nan) ok = 0;
-      else if (wbest < 0 || best.absv == 0.0) ok = 0;
+      else if (wbest < 0 || best.absv == 0.f) ok = 0;
       __syncwarp();  // orders every lane's loads after the lane that acquired the winner
       if (ok) {
         // winning column, its position, and the boundary column in one round trip
@@ -519,7 +516,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
         else if (!ok && c == 0)
           atomicOr(&a.st->flags, kFlagSingular);
         s_ok = ok;
-        s_p = (float)best.v;
+        s_p = best.v;
         s_lab = best.label;
       }
     } else if (pend_l >= 0) {
@@ -559,14 +556,16 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
       S[t * W + jj] = __fdiv_rn(v, pf);  // IEEE FP32 divide = FP64 quotient rounded
     }
     __syncthreads();  // B3
-    // rank-1 update of rows t+1.. and the pivot search of row t+1
-    cand_init(cd);
+    // rank-1 update of rows t+1.. (one warp per row) and the pivot search of row t+1
+    candf_init(cd);
     const int nj = max(0, jend - j_lo);
-    for (int e = tid; e < (bb - 1 - t) * nj; e += kPT) {
-      const int i = t + 1 + e / nj, jj = e % nj;
-      const float v = fmaf(-pcol[i], S[t * W + jj], S[i * W + jj]);
-      S[i * W + jj] = v;
-      if (i == t + 1) cand_offer(cd, (double)v, lab[jj], j_lo + jj);
+    for (int i = t + 1 + warp; i < bb; i += kPT / 32) {
+      const float ci = pcol[i];
+      for (int jj = lane; jj < nj; jj += 32) {
+        const float v = fmaf(-ci, S[t * W + jj], S[i * W + jj]);
+        S[i * W + jj] = v;
+        if (i == t + 1) candf_offer(cd, v, lab[jj], j_lo + jj);
+      }
     }
     pend_l = (l != m - 1) ? l : -1;
     pend_m = m;
@@ -578,28 +577,17 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
     F[(int64_t)(a.s0 + t) * a.ldf + j_lo + j] = S[t * W + j];
   }
   for (int j = tid; j < w_own; j += kPT) a.colperm[j_lo + j] = lab[j];
-  if (c == 0 && tid == 0 && !bad) {
+  if (c == 0 && warp == 0 && !bad) {
     // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1 (Sec. 2.4),
     // log|p| in pivot order (same Neumaier steps as per pivot)
-    for (int t = 0; t < bb; ++t) {
-      const int m = m0 - t;
-      const double pv = a.pivval[a.s0 + t];
-      const int l = a.pivpos[a.s0 + t];
-      if (pv < 0.0) sign = -sign;
-      if (((m + 1) & 1) != 0) sign = -sign;
-      if (l != m - 1) sign = -sign;
-      const double x = log(fabs(pv));
-      const double tt = sum + x;
-      if (fabs(sum) >= fabs(x))
-        comp += (sum - tt) + x;
-      else
-        comp += (x - tt) + sum;
-      sum = tt;
+    __threadfence_block();
+    panel_sign_logsum(a.pivval, a.pivpos, a.s0, bb, m0, sign, sum, comp);
+    if (lane == 0) {
+      a.st->sign = sign;
+      a.st->sum = sum;
+      a.st->comp = comp;
+      a.st->steps = a.s0 + bb;
     }
-    a.st->sign = sign;
-    a.st->sum = sum;
-    a.st->comp = comp;
-    a.st->steps = a.s0 + bb;
   }
 }
 

@@ -50,8 +50,8 @@ struct ClusterArgs {
 };
 
 struct CandSlot {
-  double absv;
-  double v;
+  float absv;
+  float v;
   int label;
   int pos;
   int nan;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   int* lab = reinterpret_cast<int*>(U + kKI * kKI);       // W labels
   __shared__ CandSlot slot[2];
   __shared__ int lastlabel[2];
-  __shared__ Cand wred[kCT / 32];
+  __shared__ CandF wred[kCT / 32];
   __shared__ int s_l, s_ok, s_lab, s_lastlab, s_nmoved;
   __shared__ float s_p;
   __shared__ int s_swap[kKI];
@@ -110,20 +110,20 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       const int m = mq - t;
       const int par = t & 1;
       // local candidate of row t
-      Cand cd;
-      cand_init(cd);
+      CandF cd;
+      candf_init(cd);
       for (int j = tid; j < w_own; j += kCT)
-        if (j_lo + j < m) cand_offer(cd, (double)S[t * W + j], lab[j], j_lo + j);
-      cand_warp_reduce(cd);
+        if (j_lo + j < m) candf_offer(cd, S[t * W + j], lab[j], j_lo + j);
+      candf_warp_reduce(cd);
       if (lane == 0) wred[warp] = cd;
       __syncthreads();
       if (warp == 0) {
-        Cand b;
+        CandF b;
         if (lane < kCT / 32)
           b = wred[lane];
         else
-          cand_init(b);
-        cand_warp_reduce(b);
+          candf_init(b);
+        candf_warp_reduce(b);
         if (lane < kb && b.pos >= 0) candcol[par * kKI + lane] = S[lane * W + (b.pos - j_lo)];
         if (m - 1 >= j_lo && m - 1 < j_hi) {
           if (lane < kb) lastcol[par * kKI + lane] = S[lane * W + (m - 1 - j_lo)];
@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       }
       cluster.sync();  // every CTA's candidate is published
       if (warp == 0) {
-        Cand best;
-        cand_init(best);
+        CandF best;
+        candf_init(best);
         int wbest = -1;
         if (lane < CL) {
           const CandSlot* rs = cluster.map_shared_rank(&slot[par], lane);
@@ -153,18 +153,16 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-          Cand o;
+          CandF o;
           o.absv = __shfl_xor_sync(0xffffffffu, best.absv, off);
           o.v = __shfl_xor_sync(0xffffffffu, best.v, off);
           o.label = __shfl_xor_sync(0xffffffffu, best.label, off);
           o.pos = __shfl_xor_sync(0xffffffffu, best.pos, off);
           o.nan = __shfl_xor_sync(0xffffffffu, best.nan, off);
           const int ow = __shfl_xor_sync(0xffffffffu, wbest, off);
-          const bool better = o.pos >= 0 && cand_better(o.absv, o.label, best);
-          cand_merge(best, o);
-          if (better) wbest = ow;
+          if (candf_merge(best, o)) wbest = ow;
         }
-        const bool ok = !best.nan && wbest >= 0 && best.absv != 0.0;
+        const bool ok = !best.nan && wbest >= 0 && best.absv != 0.f;
         // owner of the boundary position m-1
         const int owner_last = (m - 1) / W;
         if (ok && lane < kb) {
@@ -175,7 +173,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           if (!ok && c == 0) atomicOr(&a.st->flags, best.nan ? kFlagNaN : kFlagSingular);
           s_ok = ok;
           s_l = best.pos;
-          s_p = (float)best.v;
+          s_p = best.v;
           s_lab = best.label;
           s_lastlab = ok ? *cluster.map_shared_rank(&lastlabel[par], owner_last) : 0;
         }
@@ -214,9 +212,9 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       }
       __syncthreads();
       const int nj = max(0, jend - j_lo);
-      for (int e = tid; e < (kb - 1 - t) * nj; e += kCT) {
-        const int i = t + 1 + e / nj, jj = e % nj;
-        S[i * W + jj] = fmaf(-pcol[i], S[t * W + jj], S[i * W + jj]);
+      for (int i = t + 1 + warp; i < kb; i += kCT / 32) {  // one warp per row
+        const float ci = pcol[i];
+        for (int jj = lane; jj < nj; jj += 32) S[i * W + jj] = fmaf(-ci, S[t * W + jj], S[i * W + jj]);
       }
       __syncthreads();
     }
@@ -326,7 +324,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   cluster.sync();
   // labels back; the panel-wide move list for the rows outside the panel
   for (int j = tid; j < w_own; j += kCT) a.colperm[j_lo + j] = lab[j];
-  if (c == 0) {
+  if (c == 0 && warp == 0) {
     if (tid == 0) {
       int k2 = 0;
       for (int k = 0; k < s_np; ++k)
@@ -336,24 +334,12 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           ++k2;
         }
       a.moves[0] = bad ? 0 : k2;
-      if (!bad) {
-        // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
-        // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
-        for (int t = 0; t < bb; ++t) {
-          const int m = m0 - t;
-          const double pv = a.pivval[a.s0 + t];
-          const int l = a.pivpos[a.s0 + t];
-          if (pv < 0.0) sign = -sign;
-          if (((m + 1) & 1) != 0) sign = -sign;
-          if (l != m - 1) sign = -sign;
-          const double x = log(fabs(pv));
-          const double tt = sum + x;
-          if (fabs(sum) >= fabs(x))
-            comp += (sum - tt) + x;
-          else
-            comp += (x - tt) + sum;
-          sum = tt;
-        }
+    }
+    if (!bad) {
+      // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
+      // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
+      panel_sign_logsum(a.pivval, a.pivpos, a.s0, bb, m0, sign, sum, comp);
+      if (lane == 0) {
         a.st->sign = sign;
         a.st->sum = sum;
         a.st->comp = comp;

@@ -16,6 +16,7 @@
 // for r_j, one FMA per minor), so the FP64 sweep is bit-identical to a literal
 // order-preserving implementation.
 #include <algorithm>
+#include <type_traits>
 
 #include "profile.cuh"
 #include "record.cuh"
@@ -35,6 +36,26 @@ __device__ __forceinline__ T to_t(double x) {
 // IEEE FP32 divide, which equals the FP64 quotient rounded to FP32 (53 >= 2*24+2).
 __device__ __forceinline__ double div_t(double a, double p) { return a / p; }
 __device__ __forceinline__ float div_t(float a, double p) { return __fdiv_rn(a, (float)p); }
+
+__device__ __forceinline__ void cand_init_any(Cand& c) { cand_init(c); }
+__device__ __forceinline__ void cand_init_any(CandF& c) { candf_init(c); }
+__device__ __forceinline__ void cand_offer_any(Cand& c, double v, int label, int pos) {
+  cand_offer(c, v, label, pos);
+}
+__device__ __forceinline__ void cand_offer_any(CandF& c, float v, int label, int pos) {
+  candf_offer(c, v, label, pos);
+}
+__device__ __forceinline__ Cand to_cand(const Cand& c) { return c; }
+__device__ __forceinline__ Cand to_cand(const CandF& f) {
+  Cand c;
+  c.absv = f.absv;  // -1 stays -1: "no candidate"
+  c.v = f.v;
+  c.label = f.label;
+  c.pos = f.pos;
+  c.nan = f.nan;
+  c.pad = 0;
+  return c;
+}
 
 // ---------------------------------------------------------------- stage (a0)
 template <typename T, typename In>
@@ -169,8 +190,10 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = 0; k < VN; ++k) r[k] = (j0 + k < ncols) ? rrow[j0 + k] : T(0);
   }
   const bool la = lookahead && blockIdx.y == 0;
-  Cand best;
-  cand_init(best);
+  // FP32 storage searches with FP32 compares (exact; off the FP64 pipe)
+  using C = typename std::conditional<sizeof(T) == 4, CandF, Cand>::type;
+  C best;
+  cand_init_any(best);
   int i = row_begin;
   if (la && i < row_stop) {
     // the next pivot row first: update it and search it (Sec. 2.2)
@@ -182,7 +205,7 @@ __global__ void __launch_bounds__(kThreads)
       if (j < ncols) {
         const T v = fma_t(-c, r[k], row[j]);
         row[j] = v;
-        cand_offer(best, (double)v, colperm[j], j);
+        cand_offer_any(best, v, colperm[j], j);
       }
     }
     ++i;
@@ -216,8 +239,14 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   if (la) {
-    cand_block_reduce(best, red);
-    if (threadIdx.x == 0) cand[blockIdx.x] = best;
+    Cand b = to_cand(best);
+    if constexpr (sizeof(T) == 4) {
+      // reduce in FP32 first (exact), then one block reduction of the result
+      candf_warp_reduce(best);
+      b = to_cand(best);
+    }
+    cand_block_reduce(b, red);
+    if (threadIdx.x == 0) cand[blockIdx.x] = b;
   }
 }
 
