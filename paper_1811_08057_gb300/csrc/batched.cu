@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(kBT)
   int* label = reinterpret_cast<int*>(P + kKB * pw);          // n_max
   int* moved_dst = label + n_max;                             // 2 kKB
   int* moved_src = moved_dst + 2 * kKB;                       // 2 kKB
+  T* Cs = reinterpret_cast<T*>(                               // kBT x (kKB + 1) multipliers
+      (reinterpret_cast<uintptr_t>(moved_src + 2 * kKB) + 15) & ~static_cast<uintptr_t>(15));
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
   __shared__ int s_swap[kKB];
@@ -282,65 +284,72 @@ __global__ void __launch_bounds__(kBT)
           __syncwarp();
         }
       }
-      // trailing rows: one warp per pair of rows (the panel row values are read once
-      // from shared memory for both)
-      for (int i0 = s0 + bb + 2 * warp; i0 < n; i0 += 2 * (kBT / 32)) {
-        const int nr = min(2, n - i0);
-        T cm[2][kKB];
+      // trailing rows, in chunks of kBT rows:
+      //  phase 1 (one thread per row): the panel's composed column moves, then the
+      //  row's kb multipliers by forward substitution in registers -> Cs;
+      //  phase 2 (register tiles of 4 rows x 4 columns): the kb rank-1 updates in
+      //  pivot order, one FMA per element per pivot (the per-pivot operations).
+      for (int r0 = s0 + bb; r0 < n; r0 += kBT) {
+        const int R = min(kBT, n - r0);
+        if (tid < R) {
+          T* row = W + (int64_t)(r0 + tid) * ldw;
+          T mv[2 * kKB];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (u >= nr) {
+          for (int k = 0; k < 2 * kKB; ++k)
+            if (k < nmoved) mv[k] = row[moved_src[k]];
 #pragma unroll
-            for (int t = 0; t < kKB; ++t) cm[u][t] = T(0);
-            continue;
-          }
-          T* row = W + (int64_t)(i0 + u) * ldw;
-          // column exchanges of the panel, composed (at most 2 * kKB = 32 positions
-          // move: one per lane)
-          T mv = T(0);
-          if (lane < nmoved) mv = row[moved_src[lane]];
-          __syncwarp();
-          if (lane < nmoved) row[moved_dst[lane]] = mv;
-          __syncwarp();
-          // multipliers: forward substitution with U[t'][t] = P[t'][m0-1-t]
-          T a = (lane < bb) ? row[m0 - 1 - lane] : T(0);
+          for (int k = 0; k < 2 * kKB; ++k)
+            if (k < nmoved) row[moved_dst[k]] = mv[k];
+          T x[kKB];
+#pragma unroll
+          for (int t = 0; t < kKB; ++t) x[t] = (t < bb) ? row[m0 - 1 - t] : T(0);
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
             if (t < bb) {
-              const T ct = __shfl_sync(0xffffffffu, a, t);
-              cm[u][t] = ct;
-              if (lane > t && lane < bb) a = fma_t(-ct, P[t * pw + (m0 - 1 - lane)], a);
-            } else {
-              cm[u][t] = T(0);
+#pragma unroll
+              for (int t2 = t + 1; t2 < kKB; ++t2)
+                if (t2 < bb) x[t2] = fma_t(-x[t], P[t * pw + (m0 - 1 - t2)], x[t2]);
             }
           }
-          if (rec && lane < bb) row[m0 - 1 - lane] = a;  // multipliers (L) of this panel
-        }
-        // the panel's rank-1 updates, in pivot order, one register per element
-        T* row0 = W + (int64_t)i0 * ldw;
-        T* row1 = row0 + ldw;
-        if (nr == 2) {
-          for (int j = lane; j < ncols; j += 32) {
-            T v0 = row0[j], v1 = row1[j];
 #pragma unroll
-            for (int t = 0; t < kKB; ++t)
-              if (t < bb) {
-                const T r = P[t * pw + j];
-                v0 = fma_t(-cm[0][t], r, v0);
-                v1 = fma_t(-cm[1][t], r, v1);
-              }
-            row0[j] = v0;
-            row1[j] = v1;
-          }
-        } else {
-          for (int j = lane; j < ncols; j += 32) {
-            T v = row0[j];
-#pragma unroll
-            for (int t = 0; t < kKB; ++t)
-              if (t < bb) v = fma_t(-cm[0][t], P[t * pw + j], v);
-            row0[j] = v;
+          for (int t = 0; t < kKB; ++t) {
+            if (t < bb) {
+              Cs[tid * (kKB + 1) + t] = x[t];
+              if (rec) row[m0 - 1 - t] = x[t];  // multipliers (L) of this panel
+            }
           }
         }
+        __syncthreads();
+        const int nct = (ncols + 3) / 4, nrt = (R + 3) / 4;
+        for (int tile = tid; tile < nrt * nct; tile += kBT) {
+          const int ri = (tile / nct) * 4, cj = (tile % nct) * 4;
+          T acc[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              acc[i][j] = (ri + i < R && cj + j < ncols) ? W[(int64_t)(r0 + ri + i) * ldw + cj + j] : T(0);
+#pragma unroll
+          for (int t = 0; t < kKB; ++t) {
+            if (t < bb) {
+              T cv[4], rv[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) cv[i] = Cs[(ri + i) * (kKB + 1) + t];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) rv[j] = P[t * pw + cj + j];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma_t(-cv[i], rv[j], acc[i][j]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (ri + i < R && cj + j < ncols) W[(int64_t)(r0 + ri + i) * ldw + cj + j] = acc[i][j];
+        }
+        __syncthreads();
       }
       __syncthreads();
     }
@@ -379,7 +388,8 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
                       const int64_t* lda, int64_t count, int64_t n_max, double* signs,
                       double* logabs, void* const* factors, ld_mode mode, cudaStream_t stream) {
   const int64_t ldw = (int64_t)align_up((size_t)std::max<int64_t>(n_max, 1), 4);
-  const size_t smem = (size_t)kKB * (n_max + 1) * sizeof(T) + (size_t)n_max * 4 + 4 * kKB * 4 + 64;
+  const size_t smem = (size_t)kKB * (n_max + 1) * sizeof(T) + (size_t)n_max * 4 + 4 * kKB * 4 + 16 +
+                      (size_t)kBT * (kKB + 1) * sizeof(T) + 64;
   if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
   static size_t smem_set[2] = {0, 0};
   const int ti = sizeof(T) == 8;
