@@ -281,9 +281,11 @@ def run_ours(args):
 
     N = args.N
     mode = args.mode
+    stream = torch.cuda.current_stream(dev)
+    if args.workload != "dense":
+        return run_other_workload(args, pk, _lib, dev, stream, rank, world)
     A_np = workloads.dense_gaussian(N, seed=SEED, var=1.0 / N)
     A = torch.from_numpy(A_np).to(dev)
-    stream = torch.cuda.current_stream(dev)
 
     def step():
         return pk.logdet(A, mode)
@@ -395,6 +397,93 @@ def run_ours(args):
     return 0
 
 
+def run_other_workload(args, pk, _lib, dev, stream, rank, world):
+    """The batched (4096 covariance matrices) and gradient (256 x 1024^2) workloads
+    as their own benchmark line (units: dets/s and matrices/s)."""
+    import torch
+    import torch.distributed as dist
+    import workloads
+    if args.workload == "batched4096":
+        sizes = workloads.batched_sizes(4096, seed=3)
+        mats = workloads.batched_covariances_torch(sizes, seed=3, device=dev)
+        batch = pk.BatchedInputs(mats)
+        out = (torch.empty(4096, dtype=torch.float64, device=dev),
+               torch.empty(4096, dtype=torch.float64, device=dev))
+
+        def step():
+            return pk.logdet_batched(batch, "f32_plain", out=out)
+        units, unit, kernel = 4096.0, "dets/s", "batched"
+        wl = ("4096 SPD X^T X/(2n)+1e-2 I, n uniform on {32,...,512}, seed 3, FP32, "
+              "one persistent launch per step")
+        flop = float(sum(2.0 * int(n) ** 3 / 3.0 for n in sizes))
+    else:
+        B, n = 256, 1024
+        g = torch.Generator(device=dev).manual_seed(4)
+        lam = 10.0 ** (-2.0 * torch.rand(B, n, generator=g, device=dev, dtype=torch.float64))
+        Q, R = torch.linalg.qr(torch.randn(B, n, n, generator=g, device=dev, dtype=torch.float64))
+        Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
+        X = ((Q * lam[:, None, :]) @ Q.transpose(1, 2)).float()
+        del Q, R
+
+        def step():
+            Xg = X.detach().requires_grad_(True)
+            y = pk.logabsdet(Xg, "f32_plain")
+            y.sum().backward()
+            return Xg.grad
+        units, unit, kernel = float(B), "matrices/s", "batched"
+        wl = "256 SPD 1024x1024 FP32, eigenvalues log-uniform in [1e-2,1], seed 4: log|det| + gradient"
+        flop = B * (2.0 * n ** 3 / 3.0 + 2.0 * n ** 3)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    _lib.ld_profile_start(None)
+    step()
+    torch.cuda.synchronize(dev)
+    _lib.ld_profile_stop()
+    shares = {}
+    for cls in _lib.ld_profile_classes():
+        nl, tms = _lib.ld_profile_query(cls)
+        shares[cls] = {"launches": nl, "ms": round(tms, 4)}
+    clocks = ClockSampler(dev.index or 0)
+    _lib.ld_profile_start(kernel)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    _lib.ld_profile_stop()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches_all, _ = _lib.ld_profile_query(None)
+    k_launches, k_ms = _lib.ld_profile_query(kernel)
+    peaks = read_peaks()
+    # the FP32 SIMT FMA peak: 152 SMs x 128 FMA/clk x 2 flop at the sampled SM clock
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    k_flop = flop * args.steps if args.workload == "batched4096" else None
+    roof = None
+    if k_flop and k_ms > 0:
+        ach = k_flop / (k_ms * 1e-3) / 1e12
+        roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x sampled SM clock",
+                "kernel_shares": shares}
+    value = world * units / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl, "l2": "inputs larger than L2"},
+            "roofline": roof or {"kernel_shares": shares}, "tflops": flop / (ms * 1e-3) / 1e12,
+            "gpu_launches": launches_all, "clocks": clk, "cpu_baseline": None,
+            "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,6 +495,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched4096", "grad256x1024"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
