@@ -462,14 +462,15 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
     peaks = read_peaks()
     # the FP32 SIMT FMA peak: 152 SMs x 128 FMA/clk x 2 flop at the sampled SM clock
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     k_flop = flop * args.steps if args.workload == "batched4096" else None
     roof = None
     if k_flop and k_ms > 0:
         ach = k_flop / (k_ms * 1e-3) / 1e12
         roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x sampled SM clock",
+                "peak_note": "FP32 FMA: SMs x 128 lanes x 2 flop x sampled SM clock",
                 "kernel_shares": shares}
     value = world * units / (ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
