@@ -172,6 +172,57 @@ __device__ __forceinline__ void candf_warp_reduce(CandF& c) {
   }
 }
 
+// Keyed FP32 candidate for warp reductions with redux.sync, the same ordering as
+// CandF: key = bit pattern of |v| plus one (0 = no candidate; for non-NaN values
+// the order of |v| is the unsigned order of these patterns, and -0 and +0 share
+// one key), equal keys go to the smaller original label.
+struct KCand {
+  unsigned key;
+  int label;
+  int pos;
+  float v;
+  int nan;
+};
+
+__device__ __forceinline__ void kc_init(KCand& c) {
+  c.key = 0u;
+  c.label = 0x7fffffff;
+  c.pos = -1;
+  c.v = 0.f;
+  c.nan = 0;
+}
+
+__device__ __forceinline__ void kc_offer(KCand& c, float v, int label, int pos) {
+  const unsigned ab = __float_as_uint(v) & 0x7fffffffu;
+  if (ab > 0x7f800000u) {
+    c.nan = 1;
+    return;
+  }
+  const unsigned key = ab + 1u;
+  if (key > c.key || (key == c.key && label < c.label)) {
+    c.key = key;
+    c.v = v;
+    c.label = label;
+    c.pos = pos;
+  }
+}
+
+// Best candidate of the warp, delivered to every lane; returns the lane that
+// held it (any lane when no lane has a candidate).
+__device__ __forceinline__ int kc_warp_best(KCand& c) {
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, c.key);
+  const unsigned lab = (c.key == kmax) ? (unsigned)c.label : 0xffffffffu;
+  const unsigned lmin = __reduce_min_sync(0xffffffffu, lab);
+  const unsigned won = __ballot_sync(0xffffffffu, c.key == kmax && (unsigned)c.label == lmin);
+  const int src = __ffs(won) - 1;
+  c.pos = __shfl_sync(0xffffffffu, c.pos, src);
+  c.v = __shfl_sync(0xffffffffu, c.v, src);
+  c.key = kmax;
+  c.label = (int)lmin;
+  c.nan = __any_sync(0xffffffffu, c.nan);
+  return src;
+}
+
 // Sign and Neumaier log-sum of pivots [first, first + count) of a panel whose
 // first step has `m0` active columns, in pivot order: warp-parallel logs, one
 // lane adds them in order (the same operations as a per-pivot accumulation).

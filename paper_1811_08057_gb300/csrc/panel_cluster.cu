@@ -1,24 +1,30 @@
 // Panel of the blocked sweep on one thread-block cluster (FP32 storage).
 //
 // A cluster of CL CTAs (one GPC) runs all b pivot steps of the panel at rows
-// s0 .. s0+b-1 (m0 active columns). The panel is processed in inner blocks of
-// KI = 16 rows; the inner block lives in the cluster's distributed shared memory,
-// CTA c holding column positions [c*W, (c+1)*W) of its 16 rows. Per pivot row t:
-//   - each CTA searches its slice (max |a|, ties to the smallest original label,
-//     Sec. 2.2) and leaves its candidate, the candidate's column (16 values) and,
-//     if it owns position m-1, the boundary column in its own shared memory;
-//   - one cluster barrier; every CTA reads the CL candidates through DSMEM in rank
-//     order (identical reduction everywhere), then the winning and the boundary
-//     columns;
-//   - exchange of columns l and m-1 (Sec. 2.4), row t divided by p (FP64 divide,
-//     Eq. (3)), rank-1 update of the inner block's remaining rows (Eq. (2)).
+// s0 .. s0+b-1 (m0 active columns). CTA c owns column positions [c*W, (c+1)*W)
+// of the panel rows, and inside the CTA thread x owns the positions
+// c*W + x, c*W + x + 256, ...: every value of an owned position is read and
+// written by its owner only, except where a barrier separates the accesses.
+// The panel is processed in inner blocks of KI = 16 rows held in shared memory.
+// Per pivot row t (one CTA barrier, one cluster barrier):
+//   - each thread offers its positions of row t (max |a|, ties to the smallest
+//     original label, Sec. 2.2); warp and CTA reductions with redux.sync;
+//   - the CTA pushes its candidate, the candidate's column (KI values) and, if it
+//     owns position m-1, the boundary column into the shared memory of every CTA
+//     of the cluster, then arrives at the cluster barrier;
+//   - after the barrier every warp reduces the CL candidates from its own shared
+//     memory (identical everywhere), and each thread, on its own positions,
+//     exchanges columns l and m-1 (Sec. 2.4), divides row t by p (IEEE FP32
+//     divide, Eq. (3)) and applies the rank-1 update to the inner block's later
+//     rows (Eq. (2)).
 // Buffers alternate by pivot parity (rewritten only after the next barrier).
 // After an inner block, the panel rows below it receive (a) the block's column
-// exchanges composed into one move list, (b) their 16 multipliers by forward
-// substitution and (c) the block's 16 rank-1 updates applied per element in pivot
+// exchanges composed into one move list, (b) their KI multipliers by forward
+// substitution and (c) the block's KI rank-1 updates applied per element in pivot
 // order with one FMA each: every element sees the per-pivot sweep's exact
 // operations. The panel's composed moves for the rows outside the panel are
-// written to `moves` for the trailing kernels.
+// derived at the end from the change of the column labels and written to
+// `moves` for the trailing kernels.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -32,9 +38,11 @@ namespace ld {
 
 namespace {
 
-constexpr int kCT = 256;   // threads per CTA
-constexpr int kKI = 16;    // pivots per inner block
-constexpr int kBMax = 128; // largest panel
+constexpr int kCT = 256;    // threads per CTA
+constexpr int kKI = 16;     // pivots per inner block
+constexpr int kBMax = 128;  // largest panel
+constexpr int kCLMax = 16;  // largest cluster
+constexpr int kRU = 16;     // rows per register tile of the rows-below update
 
 struct ClusterArgs {
   float* F;
@@ -47,15 +55,7 @@ struct ClusterArgs {
   SweepState* st;
   float* crow;      // [kBMax][kKI] multipliers of the rows below the inner block
   int* moves;       // [1 + 2 * 2 * kBMax]: count, then (dst, src) position pairs
-};
-
-struct CandSlot {
-  float absv;
-  float v;
-  int label;
-  int pos;
-  int nan;
-  int pad;
+  int* dlist;       // [1 + 3 * 2 * kBMax]: count, then (position, new label, old label)
 };
 
 __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
@@ -69,25 +69,21 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* S = reinterpret_cast<float*>(smem_raw);          // kKI x W slice of the inner block
-  float* candcol = S + (size_t)kKI * W;                   // [2][kKI]
-  float* lastcol = candcol + 2 * kKI;                     // [2][kKI]
-  float* pcol = lastcol + 2 * kKI;                        // kKI
-  float* lcol = pcol + kKI;                               // kKI
-  float* U = lcol + kKI;                                  // kKI x kKI (block's U)
-  int* lab = reinterpret_cast<int*>(U + kKI * kKI);       // W labels
-  __shared__ CandSlot slot[2];
-  __shared__ int lastlabel[2];
-  __shared__ CandF wred[kCT / 32];
-  __shared__ int s_l, s_ok, s_lab, s_lastlab, s_nmoved;
-  __shared__ float s_p;
+  float* U = S + (size_t)kKI * W;                         // kKI x kKI (block's U)
+  float* Cm = U + kKI * kKI;                              // kBMax x kKI multipliers below
+  int* lab = reinterpret_cast<int*>(Cm + kBMax * kKI);    // W labels
+  __shared__ KCand pslot[2][kCLMax];       // candidates pushed by every CTA
+  __shared__ float pcand[2][kCLMax][kKI];  // their columns
+  __shared__ float plast[2][kKI];          // boundary column, pushed by its owner
+  __shared__ int plastlab[2];
+  __shared__ KCand wred[2][kCT / 32];
+  __shared__ int s_nmoved;
   __shared__ int s_swap[kKI];
   __shared__ int mv_dst[2 * kKI], mv_src[2 * kKI];
-  __shared__ int pmov_pos[2 * kBMax], pmov_val[2 * kBMax];  // panel-wide composition
-  __shared__ int s_np;
 
   float* F = a.F;
   for (int j = tid; j < w_own; j += kCT) lab[j] = a.colperm[j_lo + j];
-  if (tid == 0) s_np = 0;
+  if (c == 0 && tid == 0) a.dlist[0] = 0;  // read only after the cluster barriers below
   double sign = 0.0, sum = 0.0, comp = 0.0;
   if (c == 0 && tid == 0) {
     sign = a.st->sign;
@@ -95,137 +91,93 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     comp = a.st->comp;
   }
   int bad = (*reinterpret_cast<volatile int*>(&a.st->flags)) != 0;
-  __syncthreads();
 
   for (int q0 = 0; q0 < bb && !bad; q0 += kKI) {
     const int kb = min(kKI, bb - q0);
     const int mq = m0 - q0;  // active columns at the start of this inner block
-    // inner block rows into the slices
-    for (int e = tid; e < kb * w_own; e += kCT) {  // (other CTAs wrote these rows: past L1)
-      const int t = e / w_own, j = e % w_own;
-      S[t * W + j] = __ldcg(F + (int64_t)(a.s0 + q0 + t) * a.ldf + j_lo + j);
-    }
-    __syncthreads();
+    const int64_t row0 = (int64_t)(a.s0 + q0);
+    // inner block rows into the slice, own positions (other CTAs wrote some of
+    // these values: read past L1)
+    for (int t = 0; t < kb; ++t)
+      for (int j = tid; j < w_own; j += kCT) S[t * W + j] = __ldcg(F + (row0 + t) * a.ldf + j_lo + j);
     for (int t = 0; t < kb && !bad; ++t) {
       const int m = mq - t;
       const int par = t & 1;
-      // local candidate of row t
-      CandF cd;
-      candf_init(cd);
-      for (int j = tid; j < w_own; j += kCT)
-        if (j_lo + j < m) candf_offer(cd, S[t * W + j], lab[j], j_lo + j);
-      candf_warp_reduce(cd);
-      if (lane == 0) wred[warp] = cd;
+      // candidate of row t over the own positions < m, then warp and CTA best
+      KCand cd;
+      kc_init(cd);
+      const int w_act = min(w_own, m - j_lo);
+      for (int j = tid; j < w_act; j += kCT) kc_offer(cd, S[t * W + j], lab[j], j_lo + j);
+      kc_warp_best(cd);
+      if (lane == 0) wred[par][warp] = cd;
       __syncthreads();
-      if (warp == 0) {
-        CandF b;
-        if (lane < kCT / 32)
-          b = wred[lane];
-        else
-          candf_init(b);
-        candf_warp_reduce(b);
-        if (lane < kb && b.pos >= 0) candcol[par * kKI + lane] = S[lane * W + (b.pos - j_lo)];
-        if (m - 1 >= j_lo && m - 1 < j_hi) {
-          if (lane < kb) lastcol[par * kKI + lane] = S[lane * W + (m - 1 - j_lo)];
-          if (lane == 0) lastlabel[par] = lab[m - 1 - j_lo];
-        }
-        if (lane == 0) {
-          slot[par].absv = b.absv;
-          slot[par].v = b.v;
-          slot[par].label = b.label;
-          slot[par].pos = b.pos;
-          slot[par].nan = b.nan;
+      KCand cb;
+      if (lane < kCT / 32)
+        cb = wred[par][lane];
+      else
+        kc_init(cb);
+      kc_warp_best(cb);  // every warp holds the CTA's candidate
+      // push candidate, its column and the boundary column to every CTA
+      const bool own_last = (m - 1 >= j_lo) && (m - 1 < j_hi);
+      for (int e = tid; e < CL * kKI; e += kCT) {
+        const int d = e / kKI, i = e % kKI;
+        if (i < kb && cb.pos >= 0)
+          cluster.map_shared_rank(&pcand[par][c][0], d)[i] = S[i * W + (cb.pos - j_lo)];
+        if (own_last && i < kb) cluster.map_shared_rank(&plast[par][0], d)[i] = S[i * W + (m - 1 - j_lo)];
+        if (i == 0) {
+          *cluster.map_shared_rank(&pslot[par][c], d) = cb;
+          if (own_last) *cluster.map_shared_rank(&plastlab[par], d) = lab[m - 1 - j_lo];
         }
       }
-      cluster.sync();  // every CTA's candidate is published
-      if (warp == 0) {
-        CandF best;
-        candf_init(best);
-        int wbest = -1;
-        if (lane < CL) {
-          const CandSlot* rs = cluster.map_shared_rank(&slot[par], lane);
-          best.absv = rs->absv;
-          best.v = rs->v;
-          best.label = rs->label;
-          best.pos = rs->pos;
-          best.nan = rs->nan;
-          if (best.pos >= 0) wbest = lane;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          CandF o;
-          o.absv = __shfl_xor_sync(0xffffffffu, best.absv, off);
-          o.v = __shfl_xor_sync(0xffffffffu, best.v, off);
-          o.label = __shfl_xor_sync(0xffffffffu, best.label, off);
-          o.pos = __shfl_xor_sync(0xffffffffu, best.pos, off);
-          o.nan = __shfl_xor_sync(0xffffffffu, best.nan, off);
-          const int ow = __shfl_xor_sync(0xffffffffu, wbest, off);
-          if (candf_merge(best, o)) wbest = ow;
-        }
-        const bool ok = !best.nan && wbest >= 0 && best.absv != 0.f;
-        // owner of the boundary position m-1
-        const int owner_last = (m - 1) / W;
-        if (ok && lane < kb) {
-          pcol[lane] = cluster.map_shared_rank(candcol, wbest)[par * kKI + lane];
-          lcol[lane] = cluster.map_shared_rank(lastcol, owner_last)[par * kKI + lane];
-        }
-        if (lane == 0) {
-          if (!ok && c == 0) atomicOr(&a.st->flags, best.nan ? kFlagNaN : kFlagSingular);
-          s_ok = ok;
-          s_l = best.pos;
-          s_p = best.v;
-          s_lab = best.label;
-          s_lastlab = ok ? *cluster.map_shared_rank(&lastlabel[par], owner_last) : 0;
-        }
-      }
-      __syncthreads();
-      if (!s_ok) {
+      cluster.sync();  // every CTA's candidate is in every CTA
+      KCand g;
+      if (lane < CL)
+        g = pslot[par][lane];
+      else
+        kc_init(g);
+      const int wc = kc_warp_best(g);  // the winning CTA (identical in every warp)
+      const bool ok = !g.nan && g.key > 1u;
+      if (!ok) {
+        if (c == 0 && tid == 0) atomicOr(&a.st->flags, g.nan ? kFlagNaN : kFlagSingular);
         bad = 1;
         break;
       }
-      const int l = s_l;
-      const float pf = s_p;
-      const double p = (double)pf;
+      const int l = g.pos;
+      const float pf = g.v;
       if (tid == 0) s_swap[t] = l;
       if (c == 0 && tid == 0) {  // the sign and the log-sum are accumulated after the panel
-        a.pivpos[a.s0 + q0 + t] = l;
-        a.pivval[a.s0 + q0 + t] = p;
+        a.pivpos[row0 + t] = l;
+        a.pivval[row0 + t] = (double)pf;
       }
-      const bool own_l = (l >= j_lo && l < j_hi);
-      const bool own_last = (m - 1 >= j_lo) && (m - 1 < j_hi);
+      const float* pc = pcand[par][wc];  // pivot column: the multipliers of the block's rows
+      const float* lc = plast[par];      // boundary column
+      const int jl = l - j_lo, jm = m - 1 - j_lo;
       if (l != m - 1) {
-        for (int i = tid; i < kb; i += kCT) {
-          if (own_l && i != t) S[i * W + (l - j_lo)] = lcol[i];
-          if (own_last) S[i * W + (m - 1 - j_lo)] = pcol[i];
+        if (jl >= 0 && jl < w_own && jl % kCT == tid) {
+          for (int i = 0; i < kb; ++i)
+            if (i != t) S[i * W + jl] = lc[i];
+          lab[jl] = plastlab[par];
         }
-        if (tid == 0) {
-          if (own_l) lab[l - j_lo] = s_lastlab;
-          if (own_last) lab[m - 1 - j_lo] = s_lab;
+        if (jm >= 0 && jm < w_own && jm % kCT == tid) {
+          for (int i = 0; i < kb; ++i) S[i * W + jm] = pc[i];
+          lab[jm] = g.label;
         }
       }
-      const int jend = min(j_hi, m - 1);
-      for (int j = j_lo + tid; j < jend; j += kCT) {
-        const int jj = j - j_lo;
-        const float v = (j == l) ? lcol[t] : S[t * W + jj];
-        // IEEE FP32 divide: equal to the FP64 quotient rounded to FP32
-        S[t * W + jj] = __fdiv_rn(v, pf);
+      // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
+      // then the rank-1 update of the block's later rows, position by position
+      const int jend = min(w_own, m - 1 - j_lo);
+      for (int j = tid; j < jend; j += kCT) {
+        const float v = (j == jl) ? lc[t] : S[t * W + j];
+        const float r = __fdiv_rn(v, pf);
+        S[t * W + j] = r;
+        for (int i = t + 1; i < kb; ++i) S[i * W + j] = fmaf(-pc[i], r, S[i * W + j]);
       }
-      __syncthreads();
-      const int nj = max(0, jend - j_lo);
-      for (int i = t + 1 + warp; i < kb; i += kCT / 32) {  // one warp per row
-        const float ci = pcol[i];
-        for (int jj = lane; jj < nj; jj += 32) S[i * W + jj] = fmaf(-ci, S[t * W + jj], S[i * W + jj]);
-      }
-      __syncthreads();
     }
     if (bad) break;
-    // the inner block is final: back to F
-    for (int e = tid; e < kb * w_own; e += kCT) {
-      const int t = e / w_own, j = e % w_own;
-      F[(int64_t)(a.s0 + q0 + t) * a.ldf + j_lo + j] = S[t * W + j];
-    }
-    // composed column moves of this block (every CTA computes the same list) and
-    // the panel-wide composition for the rows outside the panel
+    // the inner block is final: back to F (own positions)
+    for (int t = 0; t < kb; ++t)
+      for (int j = tid; j < w_own; j += kCT) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
+    // composed column moves of this block (every CTA computes the same list)
     if (tid == 0) {
       int pos[2 * kKI], val[2 * kKI];
       int np = 0;
@@ -241,17 +193,6 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         const int tmp = val[ix];
         val[ix] = val[iy];
         val[iy] = tmp;
-        // panel-wide list
-        int px = -1, py = -1;
-        for (int k = 0; k < s_np; ++k) {
-          if (pmov_pos[k] == x) px = k;
-          if (pmov_pos[k] == y) py = k;
-        }
-        if (px < 0) { pmov_pos[s_np] = x; pmov_val[s_np] = x; px = s_np++; }
-        if (py < 0) { pmov_pos[s_np] = y; pmov_val[s_np] = y; py = s_np++; }
-        const int t2 = pmov_val[px];
-        pmov_val[px] = pmov_val[py];
-        pmov_val[py] = t2;
       }
       int k2 = 0;
       for (int k = 0; k < np; ++k)
@@ -264,28 +205,25 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     }
     cluster.sync();  // inner block written back by every CTA
     const int rows_below = bb - q0 - kb;
-    {
-      // finished inner blocks above keep the record layout: the exchanges reach them
-      const int nmoved = s_nmoved;
-      for (int r = c * (kCT / 32) + warp; r < q0; r += CL * (kCT / 32)) {
-        float* row = F + (int64_t)(a.s0 + r) * a.ldf;
-        float mvv = 0.f;
-        if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
-        __syncwarp();
-        if (lane < nmoved) row[mv_dst[lane]] = mvv;
-      }
+    const int nmoved = s_nmoved;
+    // finished inner blocks above keep the record layout: the exchanges reach them
+    for (int r = c * (kCT / 32) + warp; r < q0; r += CL * (kCT / 32)) {
+      float* row = F + (int64_t)(a.s0 + r) * a.ldf;
+      float mvv = 0.f;
+      if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
+      __syncwarp();
+      if (lane < nmoved) row[mv_dst[lane]] = mvv;
     }
     if (rows_below > 0) {
       // U block of the inner block: U[t'][t] = factored row t' at position mq-1-t
       for (int e = tid; e < kb * kb; e += kCT) {
         const int tp = e / kb, t = e % kb;
-        U[tp * kKI + t] = (tp < t) ? __ldcg(F + (int64_t)(a.s0 + q0 + tp) * a.ldf + (mq - 1 - t)) : 0.f;
+        U[tp * kKI + t] = (tp < t) ? __ldcg(F + (row0 + tp) * a.ldf + (mq - 1 - t)) : 0.f;
       }
       __syncthreads();
       // (a) moves and multipliers of the panel rows below: one warp per row
-      const int nmoved = s_nmoved;
       for (int r = c * (kCT / 32) + warp; r < rows_below; r += CL * (kCT / 32)) {
-        float* row = F + (int64_t)(a.s0 + q0 + kb + r) * a.ldf;
+        float* row = F + (row0 + kb + r) * a.ldf;
         float mvv = 0.f;
         if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
         __syncwarp();
@@ -301,50 +239,75 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           a.crow[r * kKI + lane] = x;
         }
       }
-      cluster.sync();  // multipliers visible to every CTA
-      // (b) the block's rank-1 updates on this CTA's columns, in pivot order
-      const int jend = min(j_hi, mq - kb);
-      for (int r = warp; r < rows_below; r += kCT / 32) {
-        float* row = F + (int64_t)(a.s0 + q0 + kb + r) * a.ldf;
-        float cm[kKI];
+      cluster.sync();  // multipliers and moved values visible to every CTA
+      for (int e = tid; e < rows_below * kKI; e += kCT)
+        Cm[e] = (e % kKI < kb) ? __ldcg(a.crow + e) : 0.f;
+      __syncthreads();
+      // (b) the block's rank-1 updates on the own positions, in pivot order:
+      // kRU rows per register tile, their loads in flight together
+      const int wq = max(0, min(j_hi, mq - kb) - j_lo);
+      for (int j = tid; j < wq; j += kCT) {
+        float sv[kKI];
 #pragma unroll
-        for (int t = 0; t < kKI; ++t) cm[t] = (t < kb) ? __ldcg(a.crow + r * kKI + t) : 0.f;
-        for (int j = j_lo + lane; j < jend; j += 32) {
-          float v = __ldcg(row + j);
+        for (int t = 0; t < kKI; ++t) sv[t] = (t < kb) ? S[t * W + j] : 0.f;
+        for (int r0 = 0; r0 < rows_below; r0 += kRU) {
+          float v[kRU];
 #pragma unroll
-          for (int t = 0; t < kKI; ++t)
-            if (t < kb) v = fmaf(-cm[t], S[t * W + (j - j_lo)], v);
-          row[j] = v;
+          for (int u = 0; u < kRU; ++u)
+            v[u] = (r0 + u < rows_below) ? __ldcg(F + (row0 + kb + r0 + u) * a.ldf + j_lo + j) : 0.f;
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            const float* cm = Cm + (r0 + u) * kKI;
+#pragma unroll
+            for (int t = 0; t < kKI; ++t)
+              if (t < kb) v[u] = fmaf(-cm[t], sv[t], v[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < kRU; ++u)
+            if (r0 + u < rows_below) F[(row0 + kb + r0 + u) * a.ldf + j_lo + j] = v[u];
         }
       }
+      __syncthreads();  // Cm and U are rewritten by the next block
     }
-    cluster.sync();  // rows below are up to date before the next block loads them
   }
-  // no CTA leaves while another may still read its shared memory
+  // no CTA leaves while another may still read its shared memory; the panel's
+  // rows are final
   cluster.sync();
-  // labels back; the panel-wide move list for the rows outside the panel
-  for (int j = tid; j < w_own; j += kCT) a.colperm[j_lo + j] = lab[j];
-  if (c == 0 && warp == 0) {
-    if (tid == 0) {
-      int k2 = 0;
-      for (int k = 0; k < s_np; ++k)
-        if (pmov_pos[k] != pmov_val[k]) {
-          a.moves[1 + 2 * k2] = pmov_pos[k];
-          a.moves[2 + 2 * k2] = pmov_val[k];
-          ++k2;
-        }
-      a.moves[0] = bad ? 0 : k2;
+  // labels back; changed positions for the panel-wide move list
+  for (int j = tid; j < w_own; j += kCT) {
+    const int old = a.colperm[j_lo + j], nw = lab[j];
+    if (old != nw) {
+      const int k = atomicAdd(a.dlist, 1);
+      a.dlist[1 + 3 * k] = j_lo + j;
+      a.dlist[2 + 3 * k] = nw;
+      a.dlist[3 + 3 * k] = old;
     }
-    if (!bad) {
-      // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
-      // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
-      panel_sign_logsum(a.pivval, a.pivpos, a.s0, bb, m0, sign, sum, comp);
-      if (lane == 0) {
-        a.st->sign = sign;
-        a.st->sum = sum;
-        a.st->comp = comp;
-        a.st->steps = a.s0 + bb;
-      }
+    a.colperm[j_lo + j] = nw;
+  }
+  cluster.sync();
+  if (c != 0) return;
+  // position p receives the column that started at the changed position whose
+  // old label is p's new label (the panel's exchanges restricted to the changed
+  // positions form a permutation of them)
+  const int cnt = __ldcg(a.dlist);
+  for (int e = tid; e < cnt; e += kCT) {
+    const int want = __ldcg(a.dlist + 2 + 3 * e);
+    int src = -1;
+    for (int k = 0; k < cnt; ++k)
+      if (__ldcg(a.dlist + 3 + 3 * k) == want) src = __ldcg(a.dlist + 1 + 3 * k);
+    a.moves[1 + 2 * e] = __ldcg(a.dlist + 1 + 3 * e);
+    a.moves[2 + 2 * e] = src;
+  }
+  if (tid == 0) a.moves[0] = bad ? 0 : cnt;
+  if (warp == 0 && !bad) {
+    // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
+    // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
+    panel_sign_logsum(a.pivval, a.pivpos, a.s0, bb, m0, sign, sum, comp);
+    if (lane == 0) {
+      a.st->sign = sign;
+      a.st->sum = sum;
+      a.st->comp = comp;
+      a.st->steps = a.s0 + bb;
     }
   }
 }
@@ -376,7 +339,8 @@ __global__ void apply_moves_kernel(float* __restrict__ F, int64_t ldf, int r0, i
 }  // namespace
 
 size_t panel_cluster_scratch_bytes() {
-  return align_up((size_t)kBMax * kKI * 4, kAlign) + align_up((1 + 4 * kBMax) * 4, kAlign);
+  return align_up((size_t)kBMax * kKI * 4, kAlign) + align_up((1 + 4 * kBMax) * 4, kAlign) +
+         align_up((1 + 6 * kBMax) * 4, kAlign);
 }
 
 // Launches the cluster panel for rows [s0, s0+bb) and, for the rows outside the
@@ -393,8 +357,8 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     const int CL = sizes[si];
     if (cl_ok > 0 && CL != cl_ok) continue;
     const int64_t W = ceil_div(m0, CL);
-    const size_t smem = (size_t)kKI * W * 4 + (2 * kKI * 2 + 2 * kKI) * 4 + kKI * kKI * 4 +
-                        (size_t)W * 4 + 64;
+    const size_t smem = (size_t)kKI * W * 4 + kKI * kKI * 4 + (size_t)kBMax * kKI * 4 +
+                        (size_t)W * 4;
     if (smem > 200 * 1024) continue;
     cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
@@ -421,8 +385,10 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     char* p = static_cast<char*>(scratch);
     float* crow = reinterpret_cast<float*>(p);
     int* moves = reinterpret_cast<int*>(p + align_up((size_t)kBMax * kKI * 4, kAlign));
+    int* dlist = reinterpret_cast<int*>(p + align_up((size_t)kBMax * kKI * 4, kAlign) +
+                                        align_up((1 + 4 * kBMax) * 4, kAlign));
     ClusterArgs a{static_cast<float*>(r.F), r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
-                  r.colperm, r.pivpos, r.pivval, r.state, crow, moves};
+                  r.colperm, r.pivpos, r.pivval, r.state, crow, moves, dlist};
     cudaError_t e;
     {
       ProfScope ps("panel", stream, 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
