@@ -17,6 +17,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "profile.cuh"
 #include "record.cuh"
@@ -113,6 +114,26 @@ __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int 
   }
 }
 
+// A non-blocking stream per device for work that may trail the sweep: the
+// panels' sign and log-sum (a serial FP64 chain that would otherwise sit on the
+// critical path). nullptr if it cannot be created.
+cudaStream_t side_stream() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaStream_t streams[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
 template <typename T>
 ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r, bool keep,
                         cudaStream_t stream) {
@@ -157,15 +178,48 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     }
     attr_done[es == 8] = true;
   }
+  // the cluster panels leave their sign and log-sum to a one-warp kernel on the
+  // side stream, chained in pivot order and joined before the sweep returns
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (sizeof(T) == 4 && !per_pivot && !no_cluster) {
+    side = side_stream();
+    if (side && (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      side = nullptr;
+    }
+  }
+  bool trailing = false;  // deferred work outstanding on the side stream
+  auto join = [&]() -> ld_status {
+    if (!trailing) return LD_OK;
+    trailing = false;
+    if (cudaEventRecord(ev_join, side) != cudaSuccess ||
+        cudaStreamWaitEvent(stream, ev_join, 0) != cudaSuccess)
+      return LD_ERR_CUDA;
+    return LD_OK;
+  };
   for (int64_t s0 = 0; s0 < n && st == LD_OK; s0 += b) {
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
     bool used_cluster = false;
     ld_status pst = LD_ERR_UNSUPPORTED;
     if (!per_pivot && !no_cluster && sizeof(T) == 4) {
-      pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cluster_scratch, stream);
+      pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cluster_scratch, side != nullptr, stream);
       used_cluster = (pst == LD_OK);
+      if (used_cluster && side) {
+        if (cudaEventRecord(ev_fork, stream) != cudaSuccess ||
+            cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) {
+          st = LD_ERR_CUDA;
+          break;
+        }
+        trailing = true;
+        pst = launch_panel_logsum(r, s0, bb, side);
+      }
     }
+    // a panel that accumulates its own log-sum follows the deferred ones
+    if (pst == LD_ERR_UNSUPPORTED) st = join();
+    if (st != LD_OK) break;
     if (!per_pivot && pst == LD_ERR_UNSUPPORTED)
       pst = launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, stream);
     if (pst == LD_ERR_UNSUPPORTED) {
@@ -204,6 +258,10 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     st = rankb_update(r.mode, rows, rows, bb, Cn, bb, Rt, bb, F + (s0 + bb) * r.ldf, r.ldf,
                       gemm_scratch, &r.state->flags, stream);
   }
+  const ld_status js = join();
+  if (st == LD_OK) st = js;
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   scratch_free(scratch, stream);
   return st;
 }

@@ -232,23 +232,31 @@ __device__ __forceinline__ void panel_sign_logsum(const double* pivval, const in
   const int lane = threadIdx.x & 31;
   for (int t0 = 0; t0 < count; t0 += 32) {
     const int t = t0 + lane;
-    const double x = (t < count) ? log(fabs(pivval[first + t])) : 0.0;
-    for (int k = 0; k < 32 && t0 + k < count; ++k) {
-      const double xk = __shfl_sync(0xffffffffu, x, k);
-      if (lane == 0) {
-        const int tt = t0 + k;
-        const int m = m0 - tt;
-        const double pv = pivval[first + tt];
-        const int l = pivpos[first + tt];
-        if (pv < 0.0) sign = -sign;
-        if (((m + 1) & 1) != 0) sign = -sign;
-        if (l != m - 1) sign = -sign;
-        const double s2 = sum + xk;
-        if (fabs(sum) >= fabs(xk))
-          comp += (sum - s2) + xk;
-        else
-          comp += (xk - s2) + sum;
-        sum = s2;
+    const bool valid = t < count;
+    const double pv = valid ? pivval[first + t] : 1.0;
+    const int l = valid ? pivpos[first + t] : 0;
+    const int m = m0 - t;
+    const double x = valid ? log(fabs(pv)) : 0.0;
+    // sgn(p), the Laplace sign (-1)^(1+m) and the exchange of l and m-1: the
+    // sign flips an odd number of times iff the count of flipping terms is odd
+    const int flips = (pv < 0.0) + ((m + 1) & 1) + (l != m - 1);
+    const unsigned odd = __ballot_sync(0xffffffffu, valid && (flips & 1));
+    if (__popc(odd) & 1) sign = -sign;
+    // all 32 logs into lane 0 first, then the Neumaier steps back to back (the
+    // compensation terms overlap the dependent chain of partial sums)
+    double xs[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) xs[k] = __shfl_sync(0xffffffffu, x, k);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (t0 + k < count) {
+          const double xk = xs[k];
+          const double s2 = sum + xk;
+          const double e = (fabs(sum) >= fabs(xk)) ? (sum - s2) + xk : (xk - s2) + sum;
+          comp += e;
+          sum = s2;
+        }
       }
     }
   }

@@ -6,18 +6,23 @@
 // c*W + x, c*W + x + 256, ...: every value of an owned position is read and
 // written by its owner only, except where a barrier separates the accesses.
 // The panel is processed in inner blocks of KI = 16 rows held in shared memory.
-// Per pivot row t (one CTA barrier, one cluster barrier):
+// Per pivot row t (two CTA barriers, no cluster barrier):
 //   - each thread offers its positions of row t (max |a|, ties to the smallest
 //     original label, Sec. 2.2); warp and CTA reductions with redux.sync;
 //   - the CTA pushes its candidate, the candidate's column (KI values) and, if it
 //     owns position m-1, the boundary column into the shared memory of every CTA
-//     of the cluster, then arrives at the cluster barrier;
-//   - after the barrier every warp reduces the CL candidates from its own shared
-//     memory (identical everywhere), and each thread, on its own positions,
+//     of the cluster with st.async, each CTA counting the bytes it receives on
+//     an mbarrier (a fixed number per pivot);
+//   - once its bytes are in, every warp reduces the CL candidates from its own
+//     shared memory (identical everywhere), and each thread, on its own positions,
 //     exchanges columns l and m-1 (Sec. 2.4), divides row t by p (IEEE FP32
 //     divide, Eq. (3)) and applies the rank-1 update to the inner block's later
 //     rows (Eq. (2)).
-// Buffers alternate by pivot parity (rewritten only after the next barrier).
+// Buffers and mbarriers alternate by pivot parity: a CTA pushes pivot t+2 only
+// after every CTA's pivot t+1 data reached it, which each CTA sends only after it
+// has finished with pivot t. A wait that runs out of time (it never should)
+// raises kFlagTimeout; the CTAs then skip the remaining work but keep the same
+// sequence of cluster barriers, so none leaves while another can still write to it.
 // After an inner block, the panel rows below it receive (a) the block's column
 // exchanges composed into one move list, (b) their KI multipliers by forward
 // substitution and (c) the block's KI rank-1 updates applied per element in pivot
@@ -31,6 +36,7 @@
 
 #include "profile.cuh"
 #include "record.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -42,7 +48,7 @@ constexpr int kCT = 256;    // threads per CTA
 constexpr int kKI = 16;     // pivots per inner block
 constexpr int kBMax = 128;  // largest panel
 constexpr int kCLMax = 16;  // largest cluster
-constexpr int kRU = 16;     // rows per register tile of the rows-below update
+constexpr int kRU = 8;      // rows per register tile of the rows-below update
 
 struct ClusterArgs {
   float* F;
@@ -56,8 +62,11 @@ struct ClusterArgs {
   float* crow;      // [kBMax][kKI] multipliers of the rows below the inner block
   int* moves;       // [1 + 2 * 2 * kBMax]: count, then (dst, src) position pairs
   int* dlist;       // [1 + 3 * 2 * kBMax]: count, then (position, new label, old label)
+  int logsum;       // 1: accumulate the panel's sign and log-sum here; 0: the caller does
 };
 
+// K: positions per thread (W <= K * kCT).
+template <int K>
 __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
@@ -72,10 +81,11 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   float* U = S + (size_t)kKI * W;                         // kKI x kKI (block's U)
   float* Cm = U + kKI * kKI;                              // kBMax x kKI multipliers below
   int* lab = reinterpret_cast<int*>(Cm + kBMax * kKI);    // W labels
-  __shared__ KCand pslot[2][kCLMax];       // candidates pushed by every CTA
-  __shared__ float pcand[2][kCLMax][kKI];  // their columns
-  __shared__ float plast[2][kKI];          // boundary column, pushed by its owner
+  __shared__ __align__(16) uint4 pslot[2][kCLMax];  // candidates pushed by every CTA
+  __shared__ float pcand[2][kCLMax][kKI];           // their columns
+  __shared__ float plast[2][kKI];                   // boundary column, pushed by its owner
   __shared__ int plastlab[2];
+  __shared__ __align__(8) uint64_t xbar[2];         // bytes received per pivot parity
   __shared__ KCand wred[2][kCT / 32];
   __shared__ int s_nmoved;
   __shared__ int s_swap[kKI];
@@ -91,23 +101,38 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     comp = a.st->comp;
   }
   int bad = (*reinterpret_cast<volatile int*>(&a.st->flags)) != 0;
+  if (tid == 0) {
+    tc::mbar_init(&xbar[0], 1);
+    tc::mbar_init(&xbar[1], 1);
+    tc::fence_mbar_init();
+  }
+  // bytes every CTA receives per pivot: CL candidates with their columns, the
+  // boundary column and its label
+  const uint32_t xbytes = (uint32_t)CL * (16u + 4u * kKI) + 4u * kKI + 4u;
+  cluster.sync();  // every mbarrier initialised before the first push
 
-  for (int q0 = 0; q0 < bb && !bad; q0 += kKI) {
+  for (int q0 = 0; q0 < bb; q0 += kKI) {
     const int kb = min(kKI, bb - q0);
     const int mq = m0 - q0;  // active columns at the start of this inner block
     const int64_t row0 = (int64_t)(a.s0 + q0);
     // inner block rows into the slice, own positions (other CTAs wrote some of
     // these values: read past L1)
-    for (int t = 0; t < kb; ++t)
-      for (int j = tid; j < w_own; j += kCT) S[t * W + j] = __ldcg(F + (row0 + t) * a.ldf + j_lo + j);
+    if (!bad)
+      for (int t = 0; t < kb; ++t)
+        for (int j = tid; j < w_own; j += kCT) S[t * W + j] = __ldcg(F + (row0 + t) * a.ldf + j_lo + j);
     for (int t = 0; t < kb && !bad; ++t) {
       const int m = mq - t;
-      const int par = t & 1;
+      const int gi = q0 + t;  // pivot index in the panel
+      const int par = gi & 1;
       // candidate of row t over the own positions < m, then warp and CTA best
       KCand cd;
       kc_init(cd);
       const int w_act = min(w_own, m - j_lo);
-      for (int j = tid; j < w_act; j += kCT) kc_offer(cd, S[t * W + j], lab[j], j_lo + j);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int j = tid + k * kCT;
+        if (j < w_act) kc_offer(cd, S[t * W + j], lab[j], j_lo + j);
+      }
       kc_warp_best(cd);
       if (lane == 0) wred[par][warp] = cd;
       __syncthreads();
@@ -117,24 +142,46 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       else
         kc_init(cb);
       kc_warp_best(cb);  // every warp holds the CTA's candidate
-      // push candidate, its column and the boundary column to every CTA
+      // push candidate, its column and the boundary column to every CTA (a fixed
+      // byte count: absent values are sent as zeros; a NaN in the CTA's
+      // positions is sent as the largest key)
       const bool own_last = (m - 1 >= j_lo) && (m - 1 < j_hi);
+      const uint32_t bar_l = tc::smem_u32(&xbar[par]);
       for (int e = tid; e < CL * kKI; e += kCT) {
         const int d = e / kKI, i = e % kKI;
-        if (i < kb && cb.pos >= 0)
-          cluster.map_shared_rank(&pcand[par][c][0], d)[i] = S[i * W + (cb.pos - j_lo)];
-        if (own_last && i < kb) cluster.map_shared_rank(&plast[par][0], d)[i] = S[i * W + (m - 1 - j_lo)];
+        const uint32_t rbar = tc::mapa(bar_l, d);
+        const float cv = (i < kb && cb.pos >= 0) ? S[i * W + (cb.pos - j_lo)] : 0.f;
+        tc::st_async_b32(tc::mapa(tc::smem_u32(&pcand[par][c][i]), d), __float_as_uint(cv), rbar);
+        if (own_last) {
+          const float lv = (i < kb) ? S[i * W + (m - 1 - j_lo)] : 0.f;
+          tc::st_async_b32(tc::mapa(tc::smem_u32(&plast[par][i]), d), __float_as_uint(lv), rbar);
+        }
         if (i == 0) {
-          *cluster.map_shared_rank(&pslot[par][c], d) = cb;
-          if (own_last) *cluster.map_shared_rank(&plastlab[par], d) = lab[m - 1 - j_lo];
+          tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), cb.nan ? 0xffffffffu : cb.key,
+                          (uint32_t)cb.label, (uint32_t)cb.pos, __float_as_uint(cb.v), rbar);
+          if (own_last)
+            tc::st_async_b32(tc::mapa(tc::smem_u32(&plastlab[par]), d), (uint32_t)lab[m - 1 - j_lo],
+                             rbar);
         }
       }
-      cluster.sync();  // every CTA's candidate is in every CTA
+      if (tid == 0) tc::mbar_arrive_expect_tx(&xbar[par], xbytes);
+      const bool in = tc::mbar_wait(&xbar[par], (uint32_t)((gi >> 1) & 1), &a.st->flags);
+      if (__syncthreads_or(!in)) {  // a wait ran out of time: every thread stops
+        bad = 1;
+        break;
+      }
       KCand g;
-      if (lane < CL)
-        g = pslot[par][lane];
-      else
+      if (lane < CL) {
+        const uint4 q = pslot[par][lane];
+        g.key = q.x;
+        g.label = (int)q.y;
+        g.pos = (int)q.z;
+        g.v = __uint_as_float(q.w);
+        g.nan = (q.x == 0xffffffffu);
+        if (g.nan) g.key = 0u;
+      } else {
         kc_init(g);
+      }
       const int wc = kc_warp_best(g);  // the winning CTA (identical in every warp)
       const bool ok = !g.nan && g.key > 1u;
       if (!ok) {
@@ -166,48 +213,75 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
       // then the rank-1 update of the block's later rows, position by position
       const int jend = min(w_own, m - 1 - j_lo);
-      for (int j = tid; j < jend; j += kCT) {
-        const float v = (j == jl) ? lc[t] : S[t * W + j];
-        const float r = __fdiv_rn(v, pf);
-        S[t * W + j] = r;
-        for (int i = t + 1; i < kb; ++i) S[i * W + j] = fmaf(-pc[i], r, S[i * W + j]);
+      float r[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int j = tid + k * kCT;
+        r[k] = 0.f;
+        if (j < jend) {
+          const float v = (j == jl) ? lc[t] : S[t * W + j];
+          r[k] = __fdiv_rn(v, pf);
+          S[t * W + j] = r[k];
+        }
+      }
+      for (int i = t + 1; i < kb; ++i) {
+        const float ci = pc[i];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int j = tid + k * kCT;
+          if (j < jend) S[i * W + j] = fmaf(-ci, r[k], S[i * W + j]);
+        }
       }
     }
-    if (bad) break;
+    // after a failed pivot or a timeout the CTAs only keep the barrier sequence
     // the inner block is final: back to F (own positions)
-    for (int t = 0; t < kb; ++t)
-      for (int j = tid; j < w_own; j += kCT) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
-    // composed column moves of this block (every CTA computes the same list)
-    if (tid == 0) {
-      int pos[2 * kKI], val[2 * kKI];
-      int np = 0;
+    if (!bad)
+      for (int t = 0; t < kb; ++t)
+        for (int j = tid; j < w_own; j += kCT) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
+    // composed column moves of this block (every CTA computes the same list):
+    // lane k of warp 0 holds entry k (a position and the position whose column
+    // it receives)
+    if (warp == 0 && !bad) {
+      __syncwarp();  // s_swap of the last pivot
+      int mypos = -1, myval = -1, np = 0;
+      const int sw = (lane < kb) ? s_swap[lane] : 0;
       for (int t = 0; t < kb; ++t) {
-        const int x = s_swap[t], y = mq - 1 - t;
-        int ix = -1, iy = -1;
-        for (int k = 0; k < np; ++k) {
-          if (pos[k] == x) ix = k;
-          if (pos[k] == y) iy = k;
+        const int x = __shfl_sync(0xffffffffu, sw, t), y = mq - 1 - t;
+        const unsigned bx = __ballot_sync(0xffffffffu, lane < np && mypos == x);
+        int ix = np;
+        if (bx) {
+          ix = __ffs(bx) - 1;
+        } else {
+          if (lane == np) mypos = myval = x;
+          ++np;
         }
-        if (ix < 0) { pos[np] = x; val[np] = x; ix = np++; }
-        if (iy < 0) { pos[np] = y; val[np] = y; iy = np++; }
-        const int tmp = val[ix];
-        val[ix] = val[iy];
-        val[iy] = tmp;
+        const unsigned by = __ballot_sync(0xffffffffu, lane < np && mypos == y);
+        int iy = np;
+        if (by) {
+          iy = __ffs(by) - 1;
+        } else {
+          if (lane == np) mypos = myval = y;
+          ++np;
+        }
+        const int vx = __shfl_sync(0xffffffffu, myval, ix);
+        const int vy = __shfl_sync(0xffffffffu, myval, iy);
+        if (lane == ix) myval = vy;
+        if (lane == iy) myval = vx;
       }
-      int k2 = 0;
-      for (int k = 0; k < np; ++k)
-        if (pos[k] != val[k]) {
-          mv_dst[k2] = pos[k];
-          mv_src[k2] = val[k];
-          ++k2;
-        }
-      s_nmoved = k2;
+      const bool moved = lane < np && mypos != myval;
+      const unsigned bm = __ballot_sync(0xffffffffu, moved);
+      if (moved) {
+        const int k = __popc(bm & ((1u << lane) - 1u));
+        mv_dst[k] = mypos;
+        mv_src[k] = myval;
+      }
+      if (lane == 0) s_nmoved = __popc(bm);
     }
     cluster.sync();  // inner block written back by every CTA
     const int rows_below = bb - q0 - kb;
-    const int nmoved = s_nmoved;
+    const int nmoved = bad ? 0 : s_nmoved;
     // finished inner blocks above keep the record layout: the exchanges reach them
-    for (int r = c * (kCT / 32) + warp; r < q0; r += CL * (kCT / 32)) {
+    for (int r = c * (kCT / 32) + warp; r < q0 && !bad; r += CL * (kCT / 32)) {
       float* row = F + (int64_t)(a.s0 + r) * a.ldf;
       float mvv = 0.f;
       if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
@@ -216,13 +290,13 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     }
     if (rows_below > 0) {
       // U block of the inner block: U[t'][t] = factored row t' at position mq-1-t
-      for (int e = tid; e < kb * kb; e += kCT) {
+      for (int e = tid; e < kb * kb && !bad; e += kCT) {
         const int tp = e / kb, t = e % kb;
         U[tp * kKI + t] = (tp < t) ? __ldcg(F + (row0 + tp) * a.ldf + (mq - 1 - t)) : 0.f;
       }
       __syncthreads();
       // (a) moves and multipliers of the panel rows below: one warp per row
-      for (int r = c * (kCT / 32) + warp; r < rows_below; r += CL * (kCT / 32)) {
+      for (int r = c * (kCT / 32) + warp; r < rows_below && !bad; r += CL * (kCT / 32)) {
         float* row = F + (row0 + kb + r) * a.ldf;
         float mvv = 0.f;
         if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
@@ -240,31 +314,54 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         }
       }
       cluster.sync();  // multipliers and moved values visible to every CTA
-      for (int e = tid; e < rows_below * kKI; e += kCT)
+      for (int e = tid; e < rows_below * kKI && !bad; e += kCT)
         Cm[e] = (e % kKI < kb) ? __ldcg(a.crow + e) : 0.f;
       __syncthreads();
       // (b) the block's rank-1 updates on the own positions, in pivot order:
-      // kRU rows per register tile, their loads in flight together
-      const int wq = max(0, min(j_hi, mq - kb) - j_lo);
-      for (int j = tid; j < wq; j += kCT) {
-        float sv[kKI];
+      // register tiles of kRU rows x 2 positions, their loads in flight together
+      const int wq = bad ? 0 : max(0, min(j_hi, mq - kb) - j_lo);
+      const float4* Cm4 = reinterpret_cast<const float4*>(Cm);
+      float* base = F + (row0 + kb) * a.ldf + j_lo;
+      for (int j0 = tid; j0 < wq; j0 += 2 * kCT) {
+        const int j1 = j0 + kCT;
+        const bool has1 = j1 < wq;
+        float s0v[kKI], s1v[kKI];
 #pragma unroll
-        for (int t = 0; t < kKI; ++t) sv[t] = (t < kb) ? S[t * W + j] : 0.f;
+        for (int t = 0; t < kKI; ++t) {
+          s0v[t] = (t < kb) ? S[t * W + j0] : 0.f;
+          s1v[t] = (t < kb && has1) ? S[t * W + j1] : 0.f;
+        }
         for (int r0 = 0; r0 < rows_below; r0 += kRU) {
-          float v[kRU];
-#pragma unroll
-          for (int u = 0; u < kRU; ++u)
-            v[u] = (r0 + u < rows_below) ? __ldcg(F + (row0 + kb + r0 + u) * a.ldf + j_lo + j) : 0.f;
+          float v0[kRU], v1[kRU];
 #pragma unroll
           for (int u = 0; u < kRU; ++u) {
-            const float* cm = Cm + (r0 + u) * kKI;
-#pragma unroll
-            for (int t = 0; t < kKI; ++t)
-              if (t < kb) v[u] = fmaf(-cm[t], sv[t], v[u]);
+            const bool in = r0 + u < rows_below;
+            v0[u] = in ? __ldcg(base + (int64_t)(r0 + u) * a.ldf + j0) : 0.f;
+            v1[u] = (in && has1) ? __ldcg(base + (int64_t)(r0 + u) * a.ldf + j1) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < kRU; ++u)
-            if (r0 + u < rows_below) F[(row0 + kb + r0 + u) * a.ldf + j_lo + j] = v[u];
+          for (int u = 0; u < kRU; ++u) {
+#pragma unroll
+            for (int t4 = 0; t4 < kKI / 4; ++t4) {
+              const float4 c4 = Cm4[(r0 + u) * (kKI / 4) + t4];
+              const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int t = 4 * t4 + q;
+                if (t < kb) {
+                  v0[u] = fmaf(-cc[q], s0v[t], v0[u]);
+                  v1[u] = fmaf(-cc[q], s1v[t], v1[u]);
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            if (r0 + u < rows_below) {
+              base[(int64_t)(r0 + u) * a.ldf + j0] = v0[u];
+              if (has1) base[(int64_t)(r0 + u) * a.ldf + j1] = v1[u];
+            }
+          }
         }
       }
       __syncthreads();  // Cm and U are rewritten by the next block
@@ -290,16 +387,19 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   // old label is p's new label (the panel's exchanges restricted to the changed
   // positions form a permutation of them)
   const int cnt = __ldcg(a.dlist);
+  int* dl = reinterpret_cast<int*>(Cm);  // 3 x cnt <= 3 x 2 kBMax ints
+  for (int e = tid; e < 3 * cnt; e += kCT) dl[e] = __ldcg(a.dlist + 1 + e);
+  __syncthreads();
   for (int e = tid; e < cnt; e += kCT) {
-    const int want = __ldcg(a.dlist + 2 + 3 * e);
+    const int want = dl[3 * e + 1];
     int src = -1;
     for (int k = 0; k < cnt; ++k)
-      if (__ldcg(a.dlist + 3 + 3 * k) == want) src = __ldcg(a.dlist + 1 + 3 * k);
-    a.moves[1 + 2 * e] = __ldcg(a.dlist + 1 + 3 * e);
+      if (dl[3 * k + 2] == want) src = dl[3 * k];
+    a.moves[1 + 2 * e] = dl[3 * e];
     a.moves[2 + 2 * e] = src;
   }
   if (tid == 0) a.moves[0] = bad ? 0 : cnt;
-  if (warp == 0 && !bad) {
+  if (warp == 0 && !bad && a.logsum) {
     // det A = p det A*, Laplace sign (-1)^(1+m), exchange of l and m-1
     // (Sec. 2.4), log|p| in pivot order (same Neumaier steps as per pivot)
     panel_sign_logsum(a.pivval, a.pivpos, a.s0, bb, m0, sign, sum, comp);
@@ -345,25 +445,33 @@ size_t panel_cluster_scratch_bytes() {
 
 // Launches the cluster panel for rows [s0, s0+bb) and, for the rows outside the
 // panel that must follow its column exchanges, applies the composed moves
-// (rows >= swap_row_begin other than the panel's). LD_ERR_UNSUPPORTED when the
-// cluster cannot be formed or the slice does not fit (the caller falls back).
+// (rows >= swap_row_begin other than the panel's). With defer_logsum the kernel
+// leaves the panel's sign and log-sum to launch_panel_logsum. LD_ERR_UNSUPPORTED
+// when the cluster cannot be formed or the slice does not fit (the caller falls
+// back).
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
-                               void* scratch, cudaStream_t stream) {
+                               void* scratch, bool defer_logsum, cudaStream_t stream) {
   if (r.mode == LD_F64_BLOCKED || bb > kBMax) return LD_ERR_UNSUPPORTED;
   const int64_t m0 = r.n - s0;
-  static int cl_ok = -1;  // cluster size that launched before (16 or 8), 0 = none
+  static int cl_ok = -1;  // cluster size that formed before (16 or 8), 0 = none
+  if (cl_ok == 0) return LD_ERR_UNSUPPORTED;
   const int sizes[2] = {16, 8};
+  bool tried = false;
   for (int si = 0; si < 2; ++si) {
     const int CL = sizes[si];
     if (cl_ok > 0 && CL != cl_ok) continue;
     const int64_t W = ceil_div(m0, CL);
     const size_t smem = (size_t)kKI * W * 4 + kKI * kKI * 4 + (size_t)kBMax * kKI * 4 +
                         (size_t)W * 4;
-    if (smem > 200 * 1024) continue;
-    cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    if (CL > 8)
-      cudaFuncSetAttribute(panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (smem > 200 * 1024 || W > 8 * kCT) continue;
+    const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
+    void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<1>
+                                : K == 2 ? panel_cluster_kernel<2>
+                                : K == 4 ? panel_cluster_kernel<4>
+                                         : panel_cluster_kernel<8>;
+    tried = true;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (CL > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kCT);
@@ -377,8 +485,7 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel, &cfg) != cudaSuccess ||
-        nclusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
       cudaGetLastError();
       continue;
     }
@@ -388,12 +495,13 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     int* dlist = reinterpret_cast<int*>(p + align_up((size_t)kBMax * kKI * 4, kAlign) +
                                         align_up((1 + 4 * kBMax) * 4, kAlign));
     ClusterArgs a{static_cast<float*>(r.F), r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
-                  r.colperm, r.pivpos, r.pivval, r.state, crow, moves, dlist};
+                  r.colperm, r.pivpos, r.pivval, r.state, crow, moves, dlist,
+                  defer_logsum ? 0 : 1};
     cudaError_t e;
     {
       ProfScope ps("panel", stream, 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
                    (double)bb * bb * m0);
-      e = cudaLaunchKernelEx(&cfg, panel_cluster_kernel, a);
+      e = cudaLaunchKernelEx(&cfg, kern, a);
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -412,8 +520,30 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     }
     return LD_OK;
   }
-  cl_ok = 0;
+  if (tried && cl_ok < 0) cl_ok = 0;  // no cluster of 16 or 8 forms on this device
   return LD_ERR_UNSUPPORTED;
+}
+
+// Sign and compensated log-sum of the panel's pivots (Sec. 2.4, Eq. (2)): one
+// warp, the same steps as the panel kernel's own accumulation.
+__global__ void panel_logsum_kernel(const double* __restrict__ pivval,
+                                    const int* __restrict__ pivpos, int s0, int bb, int m0,
+                                    SweepState* st) {
+  double sign = st->sign, sum = st->sum, comp = st->comp;
+  panel_sign_logsum(pivval, pivpos, s0, bb, m0, sign, sum, comp);
+  if (threadIdx.x == 0) {
+    st->sign = sign;
+    st->sum = sum;
+    st->comp = comp;
+    st->steps = s0 + bb;
+  }
+}
+
+ld_status launch_panel_logsum(const Record& r, int64_t s0, int64_t bb, cudaStream_t stream) {
+  ProfScope ps("logsum", stream, 12.0 * bb, 0.0);
+  panel_logsum_kernel<<<1, 32, 0, stream>>>(r.pivval, r.pivpos, (int)s0, (int)bb,
+                                            (int)(r.n - s0), r.state);
+  return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
 
 }  // namespace ld

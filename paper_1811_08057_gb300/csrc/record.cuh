@@ -151,7 +151,8 @@ ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row
 // ---- cluster panel kernel (panel_cluster.cu), FP32 storage ----
 size_t panel_cluster_scratch_bytes();
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
-                               void* scratch, cudaStream_t stream);
+                               void* scratch, bool defer_logsum, cudaStream_t stream);
+ld_status launch_panel_logsum(const Record& r, int64_t s0, int64_t bb, cudaStream_t stream);
 
 // ---- blocked path (blocked.cu) ----
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
