@@ -48,7 +48,7 @@ constexpr int kCT = 256;    // threads per CTA
 constexpr int kKI = 16;     // pivots per inner block
 constexpr int kBMax = 128;  // largest panel
 constexpr int kCLMax = 16;  // largest cluster
-constexpr int kRU = 8;      // rows per register tile of the rows-below update
+constexpr int kRU = 16;     // rows per register tile of the rows-below update
 
 struct ClusterArgs {
   float* F;
@@ -200,15 +200,16 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       const float* lc = plast[par];      // boundary column
       const int jl = l - j_lo, jm = m - 1 - j_lo;
       if (l != m - 1) {
-        if (jl >= 0 && jl < w_own && jl % kCT == tid) {
-          for (int i = 0; i < kb; ++i)
-            if (i != t) S[i * W + jl] = lc[i];
-          lab[jl] = plastlab[par];
+        // the warp of each owner writes the exchanged column, one row per lane
+        if (jl >= 0 && jl < w_own && (jl % kCT) / 32 == warp) {
+          if (lane < kb && lane != t) S[lane * W + jl] = lc[lane];
+          if (jl % kCT == tid) lab[jl] = plastlab[par];
         }
-        if (jm >= 0 && jm < w_own && jm % kCT == tid) {
-          for (int i = 0; i < kb; ++i) S[i * W + jm] = pc[i];
-          lab[jm] = g.label;
+        if (jm >= 0 && jm < w_own && (jm % kCT) / 32 == warp) {
+          if (lane < kb) S[lane * W + jm] = pc[lane];
+          if (jm % kCT == tid) lab[jm] = g.label;
         }
+        __syncwarp();
       }
       // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
       // then the rank-1 update of the block's later rows, position by position
@@ -224,7 +225,24 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           S[t * W + j] = r[k];
         }
       }
-      for (int i = t + 1; i < kb; ++i) {
+      // four rows at a time: their loads in flight together
+      int i = t + 1;
+      for (; i + 3 < kb; i += 4) {
+        const float c0 = pc[i], c1 = pc[i + 1], c2 = pc[i + 2], c3 = pc[i + 3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int j = tid + k * kCT;
+          if (j < jend) {
+            float* col = S + (size_t)i * W + j;
+            const float a0 = col[0], a1 = col[W], a2 = col[2 * W], a3 = col[3 * W];
+            col[0] = fmaf(-c0, r[k], a0);
+            col[W] = fmaf(-c1, r[k], a1);
+            col[2 * W] = fmaf(-c2, r[k], a2);
+            col[3 * W] = fmaf(-c3, r[k], a3);
+          }
+        }
+      }
+      for (; i < kb; ++i) {
         const float ci = pc[i];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -239,41 +257,34 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       for (int t = 0; t < kb; ++t)
         for (int j = tid; j < w_own; j += kCT) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
     // composed column moves of this block (every CTA computes the same list):
-    // lane k of warp 0 holds entry k (a position and the position whose column
-    // it receives)
+    // lane k of warp 0 takes one position the block's exchanges touched (lanes
+    // k < kb: l_k, lanes kb + k: mq-1-k; one representative per distinct
+    // position) and follows it back through the exchanges, last to first, to
+    // the position whose column it receives
     if (warp == 0 && !bad) {
       __syncwarp();  // s_swap of the last pivot
-      int mypos = -1, myval = -1, np = 0;
       const int sw = (lane < kb) ? s_swap[lane] : 0;
-      for (int t = 0; t < kb; ++t) {
+      int p = -1;
+      if (lane < kb)
+        p = sw;
+      else if (lane < 2 * kb)
+        p = mq - 1 - (lane - kb);
+      const unsigned same = __match_any_sync(0xffffffffu, p);
+      const bool rep = lane < 2 * kb && __ffs(same) - 1 == lane;
+      int src = p;
+      for (int t = kb - 1; t >= 0; --t) {
         const int x = __shfl_sync(0xffffffffu, sw, t), y = mq - 1 - t;
-        const unsigned bx = __ballot_sync(0xffffffffu, lane < np && mypos == x);
-        int ix = np;
-        if (bx) {
-          ix = __ffs(bx) - 1;
-        } else {
-          if (lane == np) mypos = myval = x;
-          ++np;
-        }
-        const unsigned by = __ballot_sync(0xffffffffu, lane < np && mypos == y);
-        int iy = np;
-        if (by) {
-          iy = __ffs(by) - 1;
-        } else {
-          if (lane == np) mypos = myval = y;
-          ++np;
-        }
-        const int vx = __shfl_sync(0xffffffffu, myval, ix);
-        const int vy = __shfl_sync(0xffffffffu, myval, iy);
-        if (lane == ix) myval = vy;
-        if (lane == iy) myval = vx;
+        if (src == x)
+          src = y;
+        else if (src == y)
+          src = x;
       }
-      const bool moved = lane < np && mypos != myval;
+      const bool moved = rep && src != p;
       const unsigned bm = __ballot_sync(0xffffffffu, moved);
       if (moved) {
         const int k = __popc(bm & ((1u << lane) - 1u));
-        mv_dst[k] = mypos;
-        mv_src[k] = myval;
+        mv_dst[k] = p;
+        mv_src[k] = src;
       }
       if (lane == 0) s_nmoved = __popc(bm);
     }
