@@ -28,11 +28,12 @@ namespace {
 
 constexpr int kPanel = 128;  // b, a multiple of 64 (tensor-core K-chunks)
 
-// Forward substitution for the multipliers of rows [row_begin, n): one warp per
-// row, lane L holds the values of pivots L, L+32, ... in registers.
+// Forward substitution for the multipliers of rows [row_begin, row_end) (into Cn,
+// row i at Cn + (i - row_begin) * bb): one warp per row, lane L holds the values
+// of pivots L, L+32, ... in registers.
 template <typename T, int KMAX>
 __global__ void __launch_bounds__(256)
-    trsm_kernel(T* __restrict__ F, int64_t ldf, int n, int s0, int bb, int m0, int row_begin,
+    trsm_kernel(T* __restrict__ F, int64_t ldf, int row_end, int s0, int bb, int m0, int row_begin,
                 T* __restrict__ Cn, const int* __restrict__ moves) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // bb x bb, U[t' * bb + t]
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
-  for (int i = row_begin + blockIdx.x * warps + (threadIdx.x >> 5); i < n;
+  for (int i = row_begin + blockIdx.x * warps + (threadIdx.x >> 5); i < row_end;
        i += gridDim.x * warps) {
     T* row = F + (int64_t)i * ldf;
     if (moves) {
@@ -114,24 +115,81 @@ __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int 
   }
 }
 
-// A non-blocking stream per device for work that may trail the sweep: the
-// panels' sign and log-sum (a serial FP64 chain that would otherwise sit on the
-// critical path). nullptr if it cannot be created.
-cudaStream_t side_stream() {
+// Streams of one device for the look-ahead pipeline of the blocked sweep:
+//   hi   (greatest priority) the critical chain: panel, then the multipliers and
+//        the update of the next panel's rows;
+//   lo   (least priority) the same for the remaining trailing rows, overlapping
+//        the next panel;
+//   aux  the panels' sign and log-sum (a serial FP64 chain).
+struct SweepStreams {
+  cudaStream_t hi = nullptr, lo = nullptr, aux = nullptr;
+};
+
+bool sweep_streams(SweepStreams* out) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
-  static cudaStream_t streams[kMaxDev] = {};
+  static SweepStreams per_dev[kMaxDev];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
-    return nullptr;
+    return false;
   }
   std::lock_guard<std::mutex> lock(mu);
-  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    streams[dev] = nullptr;
+  SweepStreams& s = per_dev[dev];
+  if (!s.hi) {
+    int least = 0, greatest = 0;
+    SweepStreams t;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&t.hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&t.lo, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&t.aux, cudaStreamNonBlocking, least) != cudaSuccess) {
+      cudaGetLastError();
+      if (t.hi) cudaStreamDestroy(t.hi);
+      if (t.lo) cudaStreamDestroy(t.lo);
+      return false;
+    }
+    s = t;
   }
-  return streams[dev];
+  *out = s;
+  return true;
+}
+
+// Stream-order link: `to` waits for the work enqueued on `from` so far.
+ld_status link(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  if (from == to) return LD_OK;
+  if (cudaEventRecord(ev, from) != cudaSuccess || cudaStreamWaitEvent(to, ev, 0) != cudaSuccess)
+    return LD_ERR_CUDA;
+  return LD_OK;
+}
+
+template <typename T>
+ld_status launch_trsm(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, int64_t row_begin,
+                      int64_t row_end, T* Cn, const int* moves, size_t smem, cudaStream_t stream) {
+  const int64_t rows = row_end - row_begin;
+  if (rows <= 0) return LD_OK;
+  const int warps = 8;
+  const int grid = (int)std::min<int64_t>(ceil_div(rows, warps), device_sm_count() * 2);
+  ProfScope ps("trsm", stream, 3.0 * sizeof(T) * (double)rows * bb, (double)rows * bb * bb);
+  trsm_kernel<T, kPanel / 32><<<grid, 256, smem, stream>>>(F, ldf, (int)row_end, (int)s0, (int)bb,
+                                                          (int)m0, (int)row_begin, Cn, moves);
+  return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
+}
+
+// Trailing update D[M x ncols] -= C[M x bb] R^T for the rows of one stream: the
+// tensor-core modes take B already in their format (ob), the FP64 mode Rt itself.
+template <typename T>
+ld_status trailing_update(ld_mode mode, int64_t M, int64_t ncols, int64_t bb, const T* C,
+                          const T* Rt, const TcOperand& ob, void* a_scratch, T* D, int64_t ldd,
+                          int* err, cudaStream_t stream) {
+  if (M <= 0 || ncols <= 0) return LD_OK;
+  if (mode == LD_F64_BLOCKED)
+    return rankb_update(mode, M, ncols, bb, C, bb, Rt, bb, D, ldd, nullptr, err, stream);
+  TcOperand oa;
+  ld_status st = rankb_prepare(mode, M, bb, reinterpret_cast<const float*>(C), bb, a_scratch, &oa,
+                               stream);
+  if (st != LD_OK) return st;
+  return rankb_tc(mode, oa, ob, (int)M, (int)ncols, (int)bb, reinterpret_cast<float*>(D), ldd, 0, 1,
+                  err, stream);
 }
 
 template <typename T>
@@ -143,30 +201,41 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);
   const size_t cn_bytes = align_up((size_t)n * b * es, kAlign);
-  const size_t panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign) +
-                             align_up(panel_cluster_scratch_bytes(), kAlign);
-  const size_t scratch_bytes =
-      2 * cn_bytes + panel_bytes + rankb_scratch_bytes(r.mode, n, n, b) + 2 * kAlign;
+  const size_t grid_panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
+  const size_t cl_bytes = align_up(panel_cluster_scratch_bytes(), kAlign);
+  const size_t bsc_bytes = align_up(rankb_operand_bytes(r.mode, n, b), kAlign);
+  const size_t anext_bytes = align_up(rankb_operand_bytes(r.mode, b, b), kAlign);
+  const size_t arest_bytes = bsc_bytes;
+  const size_t scratch_bytes = 3 * cn_bytes + grid_panel_bytes + 2 * cl_bytes + 2 * bsc_bytes +
+                               anext_bytes + arest_bytes + 2 * kAlign;
   void* scratch = nullptr;
   st = scratch_alloc(&scratch, scratch_bytes, stream);
   if (st != LD_OK) return st;
-  char* base = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
-  T* Cn = reinterpret_cast<T*>(base);
-  T* Rt = reinterpret_cast<T*>(base + cn_bytes);
-  void* panel_scratch = base + 2 * cn_bytes;
-  void* cluster_scratch =
-      base + 2 * cn_bytes + align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
-  const int* cluster_moves = reinterpret_cast<const int*>(
-      static_cast<char*>(cluster_scratch) + align_up((size_t)128 * 16 * 4, kAlign));
+  char* p = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
+  T* Cn[2] = {reinterpret_cast<T*>(p), reinterpret_cast<T*>(p + cn_bytes)};
+  p += 2 * cn_bytes;
+  T* Rt = reinterpret_cast<T*>(p);
+  p += cn_bytes;
+  void* panel_scratch = p;
+  p += grid_panel_bytes;
+  char* cl_scratch[2] = {p, p + cl_bytes};
+  p += 2 * cl_bytes;
+  char* bsc[2] = {p, p + bsc_bytes};
+  p += 2 * bsc_bytes;
+  char* anext = p;
+  p += anext_bytes;
+  char* arest = p;
+  // offset of the move list in the cluster panel's scratch
+  const size_t moves_off = align_up((size_t)128 * 16 * 4, kAlign);
   // LD_PANEL=grid selects the grid-wide panel kernel instead of the cluster one
   const char* pk = getenv("LD_PANEL");
   const bool no_cluster = pk && pk[0] == 'g';
-  void* gemm_scratch = base + 2 * cn_bytes + panel_bytes;
   // LD_PANEL_PER_PIVOT=1 runs the panel as one launch pair per pivot (the plain
   // kernels restricted to the panel rows) instead of the persistent panel kernel
   const char* pp = getenv("LD_PANEL_PER_PIVOT");
   const bool per_pivot = pp && pp[0] == '1';
   T* F = static_cast<T*>(r.F);
+  int* err = &r.state->flags;
   const size_t trsm_smem = (size_t)b * b * es;
   static bool attr_done[2] = {false, false};
   if (!attr_done[es == 8]) {
@@ -178,90 +247,109 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     }
     attr_done[es == 8] = true;
   }
-  // the cluster panels leave their sign and log-sum to a one-warp kernel on the
-  // side stream, chained in pivot order and joined before the sweep returns
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  if (sizeof(T) == 4 && !per_pivot && !no_cluster) {
-    side = side_stream();
-    if (side && (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                 cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+  // streams and events of the pipeline (everything on the caller's stream when
+  // they cannot be had)
+  SweepStreams ss;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, hi->lo, lo->hi, hi->aux
+  bool piped = sweep_streams(&ss);
+  for (int i = 0; i < 4 && piped; ++i)
+    if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
-      side = nullptr;
+      piped = false;
     }
-  }
-  bool trailing = false;  // deferred work outstanding on the side stream
-  auto join = [&]() -> ld_status {
-    if (!trailing) return LD_OK;
-    trailing = false;
-    if (cudaEventRecord(ev_join, side) != cudaSuccess ||
-        cudaStreamWaitEvent(stream, ev_join, 0) != cudaSuccess)
-      return LD_ERR_CUDA;
-    return LD_OK;
-  };
-  for (int64_t s0 = 0; s0 < n && st == LD_OK; s0 += b) {
+  if (!piped) ss.hi = ss.lo = ss.aux = stream;
+  cudaStream_t hi = ss.hi, lo = ss.lo, aux = ss.aux;
+  st = link(stream, hi, ev[0]);
+  bool rest_pending = false;  // lo holds trailing work the next panel's rows need
+  bool aux_pending = false;   // aux holds deferred log-sums
+  for (int64_t s0 = 0, k = 0; s0 < n && st == LD_OK; s0 += b, ++k) {
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
+    const int par = (int)(k & 1);
+    const int* moves = reinterpret_cast<const int*>(cl_scratch[par] + moves_off);
     bool used_cluster = false;
     ld_status pst = LD_ERR_UNSUPPORTED;
     if (!per_pivot && !no_cluster && sizeof(T) == 4) {
-      pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cluster_scratch, side != nullptr, stream);
+      pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cl_scratch[par], aux != hi, hi);
       used_cluster = (pst == LD_OK);
-      if (used_cluster && side) {
-        if (cudaEventRecord(ev_fork, stream) != cudaSuccess ||
-            cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) {
-          st = LD_ERR_CUDA;
-          break;
-        }
-        trailing = true;
-        pst = launch_panel_logsum(r, s0, bb, side);
+      if (used_cluster && aux != hi) {
+        st = link(hi, aux, ev[3]);
+        if (st != LD_OK) break;
+        aux_pending = true;
+        pst = launch_panel_logsum(r, s0, bb, aux);
       }
     }
-    // a panel that accumulates its own log-sum follows the deferred ones
-    if (pst == LD_ERR_UNSUPPORTED) st = join();
-    if (st != LD_OK) break;
-    if (!per_pivot && pst == LD_ERR_UNSUPPORTED)
-      pst = launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, stream);
     if (pst == LD_ERR_UNSUPPORTED) {
-      if (s0 > 0) st = launch_row_argmax<T>(r, s0, m0, stream);
-      for (int64_t t = 0; t < bb && st == LD_OK; ++t) {
-        const int64_t s = s0 + t;
-        st = launch_pivot_factor<T>(r, s, keep ? 0 : s0, stream);
-        if (st == LD_OK && t + 1 < bb) st = launch_update<T>(r, s, s0 + bb, true, stream);
+      // the other panel kernels exchange columns in the rows below themselves
+      // and accumulate their own log-sum: everything before them first
+      if (rest_pending) st = link(lo, hi, ev[2]);
+      if (st == LD_OK && aux_pending) st = link(aux, hi, ev[2]);
+      rest_pending = aux_pending = false;
+      if (st != LD_OK) break;
+      if (!per_pivot) pst = launch_panel<T>(r, s0, bb, keep ? 0 : s0, panel_scratch, hi);
+      if (pst == LD_ERR_UNSUPPORTED) {
+        pst = LD_OK;
+        if (s0 > 0) pst = launch_row_argmax<T>(r, s0, m0, hi);
+        for (int64_t t = 0; t < bb && pst == LD_OK; ++t) {
+          const int64_t s = s0 + t;
+          pst = launch_pivot_factor<T>(r, s, keep ? 0 : s0, hi);
+          if (pst == LD_OK && t + 1 < bb) pst = launch_update<T>(r, s, s0 + bb, true, hi);
+        }
       }
-    } else {
-      st = pst;
     }
+    st = pst;
     const int64_t rows = n - s0 - bb;
     if (st != LD_OK || rows <= 0) continue;
+    const int64_t nb = std::min<int64_t>(b, rows);  // rows of the next panel
+    const int64_t rest = rows - nb;
+    const int64_t ncols = rows;
+    // the next panel's rows were in the previous step's remaining rows
+    if (rest_pending) {
+      st = link(lo, hi, ev[2]);
+      rest_pending = false;
+      if (st != LD_OK) break;
+    }
+    const int* mv = used_cluster ? moves : nullptr;
+    st = launch_trsm<T>(F, r.ldf, s0, bb, m0, s0 + bb, s0 + bb + nb, Cn[par], mv, trsm_smem, hi);
+    if (st != LD_OK) break;
     {
-      const int warps = 8;
-      const int grid = (int)std::min<int64_t>(ceil_div(rows, warps), device_sm_count() * 2);
-      ProfScope ps("trsm", stream, 3.0 * es * (double)rows * bb, (double)rows * bb * bb);
-      trsm_kernel<T, kPanel / 32><<<grid, 256, trsm_smem, stream>>>(
-          F, r.ldf, (int)n, (int)s0, (int)bb, (int)m0, (int)(s0 + bb), Cn,
-          used_cluster ? cluster_moves : nullptr);
+      dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(bb, 32));
+      ProfScope ps("transpose", hi, 2.0 * es * (double)ncols * bb, 0.0);
+      transpose_rows_kernel<T><<<grid, 256, 0, hi>>>(F, r.ldf, (int)s0, (int)bb, (int)ncols, Rt);
+      if (cudaGetLastError() != cudaSuccess) {
+        st = LD_ERR_CUDA;
+        break;
+      }
     }
-    if (cudaGetLastError() != cudaSuccess) {
-      st = LD_ERR_CUDA;
-      break;
+    TcOperand ob{nullptr, nullptr, bb, 0};
+    if (r.mode != LD_F64_BLOCKED) {
+      st = rankb_prepare(r.mode, ncols, bb, reinterpret_cast<const float*>(Rt), bb, bsc[par], &ob, hi);
+      if (st != LD_OK) break;
     }
-    {
-      dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(bb, 32));
-      ProfScope ps("transpose", stream, 2.0 * es * (double)rows * bb, 0.0);
-      transpose_rows_kernel<T><<<grid, 256, 0, stream>>>(F, r.ldf, (int)s0, (int)bb, (int)rows, Rt);
+    // the remaining rows on lo: moves, multipliers and update, overlapping the
+    // next panel (they need this panel's moves, Rt and B, all on hi by now)
+    if (rest > 0) {
+      st = link(hi, lo, ev[1]);
+      if (st == LD_OK)
+        st = launch_trsm<T>(F, r.ldf, s0, bb, m0, s0 + bb + nb, n, Cn[par] + nb * bb, mv,
+                            trsm_smem, lo);
+      if (st == LD_OK)
+        st = trailing_update<T>(r.mode, rest, ncols, bb, Cn[par] + nb * bb, Rt, ob, arest,
+                                F + (s0 + bb + nb) * r.ldf, r.ldf, err, lo);
+      if (st != LD_OK) break;
+      rest_pending = true;
     }
-    if (cudaGetLastError() != cudaSuccess) {
-      st = LD_ERR_CUDA;
-      break;
-    }
-    st = rankb_update(r.mode, rows, rows, bb, Cn, bb, Rt, bb, F + (s0 + bb) * r.ldf, r.ldf,
-                      gemm_scratch, &r.state->flags, stream);
+    // the next panel's rows on hi
+    st = trailing_update<T>(r.mode, nb, ncols, bb, Cn[par], Rt, ob, anext, F + (s0 + bb) * r.ldf,
+                            r.ldf, err, hi);
   }
-  const ld_status js = join();
-  if (st == LD_OK) st = js;
-  if (ev_fork) cudaEventDestroy(ev_fork);
-  if (ev_join) cudaEventDestroy(ev_join);
+  // join every stream back into the caller's stream
+  const ld_status j1 = link(hi, stream, ev[0]);
+  const ld_status j2 = link(lo, stream, ev[1]);
+  const ld_status j3 = link(aux, stream, ev[2]);
+  if (st == LD_OK) st = (j1 != LD_OK) ? j1 : (j2 != LD_OK) ? j2 : j3;
+  for (int i = 0; i < 4; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   scratch_free(scratch, stream);
   return st;
 }

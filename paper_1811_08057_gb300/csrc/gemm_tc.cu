@@ -364,46 +364,50 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
     return LD_OK;
   }
   if (K % 64 != 0) return LD_ERR_UNSUPPORTED;
+  char* p = static_cast<char*>(scratch);
+  TcOperand oa, ob;
+  ld_status st = rankb_prepare(mode, M, K, static_cast<const float*>(A), lda, p, &oa, stream);
+  if (st != LD_OK) return st;
+  st = rankb_prepare(mode, N, K, static_cast<const float*>(B), ldb,
+                     p + rankb_operand_bytes(mode, M, K), &ob, stream);
+  if (st != LD_OK) return st;
+  return rankb_tc(mode, oa, ob, (int)M, (int)N, (int)K, static_cast<float*>(D), ldd, 0, 1, err,
+                  stream);
+}
+
+size_t rankb_operand_bytes(ld_mode mode, int64_t rows, int64_t K) {
+  if (mode == LD_F64_BLOCKED) return 0;
+  const size_t es = (mode == LD_F32_BF16X3) ? 2 : 4;
+  const size_t parts = (mode == LD_F32_TF32) ? 1 : 2;
+  return align_up((size_t)rows * K * es, kAlign) * parts;
+}
+
+ld_status rankb_prepare(ld_mode mode, int64_t rows, int64_t K, const float* src, int64_t ld,
+                        void* dst, TcOperand* op, cudaStream_t stream) {
   const size_t es = (mode == LD_F32_BF16X3) ? 2 : 4;
   const bool two = mode != LD_F32_TF32;
-  char* p = static_cast<char*>(scratch);
-  char* ah = p;
-  p += align_up((size_t)M * K * es, kAlign);
-  char* al = two ? p : nullptr;
-  if (two) p += align_up((size_t)M * K * es, kAlign);
-  char* bh = p;
-  p += align_up((size_t)N * K * es, kAlign);
-  char* bl = two ? p : nullptr;
-  const int sm = device_sm_count();
-  const int gA = (int)std::min<int64_t>(sm * 4, ceil_div(M * K, 256));
-  const int gB = (int)std::min<int64_t>(sm * 4, ceil_div(N * K, 256));
-  {
-    ProfScope ps("split", stream, (double)(M + N) * K * (4.0 + (two ? 2.0 : 1.0) * es), 0.0);
-    if (mode == LD_F32_BF16X3) {
-      split_kernel<kBF16x3, __nv_bfloat16><<<gA, 256, 0, stream>>>(
-          static_cast<const float*>(A), lda, (int)M, (int)K, reinterpret_cast<__nv_bfloat16*>(ah),
-          reinterpret_cast<__nv_bfloat16*>(al));
-      split_kernel<kBF16x3, __nv_bfloat16><<<gB, 256, 0, stream>>>(
-          static_cast<const float*>(B), ldb, (int)N, (int)K, reinterpret_cast<__nv_bfloat16*>(bh),
-          reinterpret_cast<__nv_bfloat16*>(bl));
-    } else if (mode == LD_F32_3XTF32) {
-      split_kernel<kTF32x3, float><<<gA, 256, 0, stream>>>(static_cast<const float*>(A), lda,
-                                                           (int)M, (int)K, reinterpret_cast<float*>(ah),
-                                                           reinterpret_cast<float*>(al));
-      split_kernel<kTF32x3, float><<<gB, 256, 0, stream>>>(static_cast<const float*>(B), ldb,
-                                                           (int)N, (int)K, reinterpret_cast<float*>(bh),
-                                                           reinterpret_cast<float*>(bl));
-    } else {
-      split_kernel<kTF32, float><<<gA, 256, 0, stream>>>(static_cast<const float*>(A), lda, (int)M,
-                                                         (int)K, reinterpret_cast<float*>(ah), nullptr);
-      split_kernel<kTF32, float><<<gB, 256, 0, stream>>>(static_cast<const float*>(B), ldb, (int)N,
-                                                         (int)K, reinterpret_cast<float*>(bh), nullptr);
-    }
+  char* hi = static_cast<char*>(dst);
+  char* lo = two ? hi + align_up((size_t)rows * K * es, kAlign) : nullptr;
+  *op = TcOperand{hi, lo, K, 0};
+  if (rows <= 0 || K <= 0) return LD_OK;
+  const int g = (int)std::min<int64_t>(device_sm_count() * 4, ceil_div(rows * K, 256));
+  ProfScope ps("split", stream, (double)rows * K * (4.0 + (two ? 2.0 : 1.0) * es), 0.0);
+  if (mode == LD_F32_BF16X3) {
+    split_kernel<kBF16x3, __nv_bfloat16><<<g, 256, 0, stream>>>(
+        src, ld, (int)rows, (int)K, reinterpret_cast<__nv_bfloat16*>(hi),
+        reinterpret_cast<__nv_bfloat16*>(lo));
+  } else if (mode == LD_F32_3XTF32) {
+    split_kernel<kTF32x3, float><<<g, 256, 0, stream>>>(src, ld, (int)rows, (int)K,
+                                                        reinterpret_cast<float*>(hi),
+                                                        reinterpret_cast<float*>(lo));
+  } else if (mode == LD_F32_TF32) {
+    split_kernel<kTF32, float><<<g, 256, 0, stream>>>(src, ld, (int)rows, (int)K,
+                                                      reinterpret_cast<float*>(hi), nullptr);
+  } else {
+    return LD_ERR_INVALID_ARG;
   }
   LD_CHECK_LAUNCH();
-  float* Df = static_cast<float*>(D);
-  const TcOperand oa{ah, al, K, 0}, ob{bh, bl, K, 0};
-  return rankb_tc(mode, oa, ob, (int)M, (int)N, (int)K, Df, ldd, 0, 1, err, stream);
+  return LD_OK;
 }
 
 // Tensor-core update on operands already in the mode's format (hi / lo parts),

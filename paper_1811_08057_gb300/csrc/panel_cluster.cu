@@ -48,7 +48,7 @@ constexpr int kCT = 256;    // threads per CTA
 constexpr int kKI = 16;     // pivots per inner block
 constexpr int kBMax = 128;  // largest panel
 constexpr int kCLMax = 16;  // largest cluster
-constexpr int kRU = 16;     // rows per register tile of the rows-below update
+constexpr int kRU = 8;      // rows per register tile of the rows-below update
 
 struct ClusterArgs {
   float* F;
@@ -269,11 +269,11 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         p = sw;
       else if (lane < 2 * kb)
         p = mq - 1 - (lane - kb);
-      const unsigned same = __match_any_sync(0xffffffffu, p);
-      const bool rep = lane < 2 * kb && __ffs(same) - 1 == lane;
+      bool rep = lane < 2 * kb;
       int src = p;
       for (int t = kb - 1; t >= 0; --t) {
         const int x = __shfl_sync(0xffffffffu, sw, t), y = mq - 1 - t;
+        if ((t < lane && x == p) || (kb + t < lane && y == p)) rep = false;
         if (src == x)
           src = y;
         else if (src == y)
@@ -342,13 +342,28 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           s0v[t] = (t < kb) ? S[t * W + j0] : 0.f;
           s1v[t] = (t < kb && has1) ? S[t * W + j1] : 0.f;
         }
+        // the next chunk's loads are issued before this chunk's FMAs
+        float n0[kRU], n1[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          const bool in = u < rows_below;
+          n0[u] = in ? __ldcg(base + (int64_t)u * a.ldf + j0) : 0.f;
+          n1[u] = (in && has1) ? __ldcg(base + (int64_t)u * a.ldf + j1) : 0.f;
+        }
         for (int r0 = 0; r0 < rows_below; r0 += kRU) {
           float v0[kRU], v1[kRU];
 #pragma unroll
           for (int u = 0; u < kRU; ++u) {
-            const bool in = r0 + u < rows_below;
-            v0[u] = in ? __ldcg(base + (int64_t)(r0 + u) * a.ldf + j0) : 0.f;
-            v1[u] = (in && has1) ? __ldcg(base + (int64_t)(r0 + u) * a.ldf + j1) : 0.f;
+            v0[u] = n0[u];
+            v1[u] = n1[u];
+          }
+          if (r0 + kRU < rows_below) {
+#pragma unroll
+            for (int u = 0; u < kRU; ++u) {
+              const bool in = r0 + kRU + u < rows_below;
+              n0[u] = in ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j0) : 0.f;
+              n1[u] = (in && has1) ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j1) : 0.f;
+            }
           }
 #pragma unroll
           for (int u = 0; u < kRU; ++u) {

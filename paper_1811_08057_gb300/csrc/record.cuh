@@ -135,6 +135,12 @@ ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, 
                    float* D, int64_t ldd, int64_t dstride, int batch, int* err,
                    cudaStream_t stream);
 size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K);
+// Bytes of one rows x K operand in the mode's tensor-core format (hi, then lo).
+size_t rankb_operand_bytes(ld_mode mode, int64_t rows, int64_t K);
+// Converts a rows x K FP32 operand (rows `ld` apart) into the mode's format at
+// dst (rankb_operand_bytes bytes) and describes it in *op.
+ld_status rankb_prepare(ld_mode mode, int64_t rows, int64_t K, const float* src, int64_t ld,
+                        void* dst, TcOperand* op, cudaStream_t stream);
 ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                        const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
                        cudaStream_t stream);
