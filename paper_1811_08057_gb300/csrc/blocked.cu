@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "profile.cuh"
 #include "record.cuh"
 
@@ -28,79 +30,107 @@ namespace {
 
 constexpr int kPanel = 128;  // b, a multiple of 64 (tensor-core K-chunks)
 
-// Forward substitution for the multipliers of rows [row_begin, row_end) (into Cn,
-// row i at Cn + (i - row_begin) * bb): one warp per row, lane L holds the values
-// of pivots L, L+32, ... in registers.
-template <typename T, int KMAX>
+// Output format of the multipliers and the transposed panel rows: the storage
+// type itself (FP64 SIMT update), or the tensor-core operand parts of the mode.
+enum OpOut { kOutT = 0, kOutTF32 = 1, kOutTF32x3 = 2, kOutBF16x3 = 3 };
+
+// Writes x as element idx of an operand in format OUT (hi, and lo for the split
+// formats; the same splits as the tensor-core path's operand preparation).
+template <int OUT, typename T>
+__device__ __forceinline__ void put_operand(void* hi, void* lo, int64_t idx, T x) {
+  if constexpr (OUT == kOutT) {
+    static_cast<T*>(hi)[idx] = x;
+  } else if constexpr (OUT == kOutTF32) {
+    static_cast<float*>(hi)[idx] = tf32_rna((float)x);
+  } else if constexpr (OUT == kOutTF32x3) {
+    float h, l;
+    tf32_split((float)x, h, l);
+    static_cast<float*>(hi)[idx] = h;
+    static_cast<float*>(lo)[idx] = l;
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    static_cast<__nv_bfloat16*>(hi)[idx] = h;
+    static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn((float)x - __bfloat162float(h));
+  }
+}
+
+// Forward substitution for the multipliers of rows [row_begin, row_end): one
+// warp per row, lane L holding the values of pivots L, L+32, ... in registers.
+// The multipliers go to F (the factor record) and, as the update's A operand
+// (row i at (i - row_begin) * bb), to ahi / alo in format OUT. One row per warp
+// and short-lived CTAs, so a concurrent critical-path kernel finds free SMs.
+template <typename T, int KMAX, int OUT>
 __global__ void __launch_bounds__(256)
     trsm_kernel(T* __restrict__ F, int64_t ldf, int row_end, int s0, int bb, int m0, int row_begin,
-                T* __restrict__ Cn, const int* __restrict__ moves) {
+                void* __restrict__ ahi, void* __restrict__ alo, const int* __restrict__ moves) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // bb x bb, U[t' * bb + t]
-  for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
-    const int tp = e / bb, t = e % bb;
+  // U[t'][t] = factored row t' at the column of pivot t (t' < t), zero elsewhere
+  const int tot = bb * bb;
+#pragma unroll 16
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int tp = e / bb, t = e - tp * bb;
     U[e] = (tp < t) ? F[(int64_t)(s0 + tp) * ldf + (m0 - 1 - t)] : T(0);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int warps = blockDim.x >> 5;
-  for (int i = row_begin + blockIdx.x * warps + (threadIdx.x >> 5); i < row_end;
-       i += gridDim.x * warps) {
-    T* row = F + (int64_t)i * ldf;
-    if (moves) {
-      // the panel's column exchanges, composed (moves[0] pairs of (dst, src))
-      const int nm = moves[0];
-      T v[8];
+  const int i = row_begin + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= row_end) return;
+  T* row = F + (int64_t)i * ldf;
+  if (moves) {
+    // the panel's column exchanges, composed (moves[0] pairs of (dst, src))
+    const int nm = moves[0];
+    T v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = lane + 32 * q;
-        v[q] = (k < nm) ? row[moves[2 + 2 * k]] : T(0);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = lane + 32 * q;
-        if (k < nm) row[moves[1 + 2 * k]] = v[q];
-      }
-      __syncwarp();
+    for (int q = 0; q < 8; ++q) {
+      const int k = lane + 32 * q;
+      v[q] = (k < nm) ? row[moves[2 + 2 * k]] : T(0);
     }
-    T a[KMAX];
+    __syncwarp();
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      const int t = lane + 32 * k;
-      a[k] = (t < bb) ? row[m0 - 1 - t] : T(0);
+    for (int q = 0; q < 8; ++q) {
+      const int k = lane + 32 * q;
+      if (k < nm) row[moves[1 + 2 * k]] = v[q];
     }
+    __syncwarp();
+  }
+  T a[KMAX];
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
-      if (kk * 32 < bb) {
-        for (int tt = 0; tt < 32; ++tt) {
-          const int t = kk * 32 + tt;
-          if (t >= bb) break;
-          const T c = __shfl_sync(0xffffffffu, a[kk], tt);
+  for (int k = 0; k < KMAX; ++k) {
+    const int t = lane + 32 * k;
+    a[k] = (t < bb) ? row[m0 - 1 - t] : T(0);
+  }
 #pragma unroll
-          for (int k = kk; k < KMAX; ++k) {
-            const int t2 = lane + 32 * k;
-            if (t2 > t && t2 < bb) a[k] = fma_t(-c, U[t * bb + t2], a[k]);
-          }
+  for (int kk = 0; kk < KMAX; ++kk) {
+    if (kk * 32 < bb) {
+      for (int tt = 0; tt < 32; ++tt) {
+        const int t = kk * 32 + tt;
+        if (t >= bb) break;
+        const T c = __shfl_sync(0xffffffffu, a[kk], tt);
+#pragma unroll
+        for (int k = kk; k < KMAX; ++k) {
+          const int t2 = lane + 32 * k;
+          if (t2 > t && t2 < bb) a[k] = fma_t(-c, U[t * bb + t2], a[k]);
         }
       }
     }
-    T* crow = Cn + (int64_t)(i - row_begin) * bb;
+  }
+  const int64_t base = (int64_t)(i - row_begin) * bb;
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      const int t = lane + 32 * k;
-      if (t < bb) {
-        row[m0 - 1 - t] = a[k];
-        crow[t] = a[k];
-      }
+  for (int k = 0; k < KMAX; ++k) {
+    const int t = lane + 32 * k;
+    if (t < bb) {
+      row[m0 - 1 - t] = a[k];
+      put_operand<OUT, T>(ahi, alo, base + t, a[k]);
     }
   }
 }
 
-// Rt[j][t] = F[s0 + t][j] for j < ncols, t < bb (32 x 32 tiles through shared memory).
-template <typename T>
+// Rt[j][t] = F[s0 + t][j] for j < ncols, t < bb (32 x 32 tiles through shared
+// memory), written in format OUT: the update's B operand.
+template <typename T, int OUT>
 __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int s0, int bb,
-                                      int ncols, T* __restrict__ Rt) {
+                                      int ncols, void* __restrict__ bhi, void* __restrict__ blo) {
   __shared__ T tile[32][33];
   const int j0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
@@ -111,7 +141,7 @@ __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int 
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
     const int j = j0 + k, t = t0 + tx;
-    if (j < ncols && t < bb) Rt[(int64_t)j * bb + t] = tile[tx][k];
+    if (j < ncols && t < bb) put_operand<OUT, T>(bhi, blo, (int64_t)j * bb + t, tile[tx][k]);
   }
 }
 
@@ -162,32 +192,108 @@ ld_status link(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
   return LD_OK;
 }
 
-template <typename T>
-ld_status launch_trsm(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, int64_t row_begin,
-                      int64_t row_end, T* Cn, const int* moves, size_t smem, cudaStream_t stream) {
+// Operand buffers of the trailing update: `cap` rows of bb elements in the
+// format of the mode (hi part, then the lo part for the split formats).
+struct OpBuf {
+  char* hi;
+  char* lo;
+  size_t es;  // bytes per element of one part
+};
+
+size_t op_elem_bytes(ld_mode mode) {
+  return mode == LD_F64_BLOCKED ? 8 : mode == LD_F32_BF16X3 ? 2 : 4;
+}
+bool op_split(ld_mode mode) { return mode == LD_F32_3XTF32 || mode == LD_F32_BF16X3; }
+size_t op_bytes(ld_mode mode, int64_t cap, int64_t bb) {
+  const size_t part = align_up((size_t)cap * bb * op_elem_bytes(mode), kAlign);
+  return op_split(mode) ? 2 * part : part;
+}
+OpBuf op_buf(ld_mode mode, char* base, int64_t cap, int64_t bb) {
+  const size_t part = align_up((size_t)cap * bb * op_elem_bytes(mode), kAlign);
+  return OpBuf{base, op_split(mode) ? base + part : nullptr, op_elem_bytes(mode)};
+}
+
+template <typename T, int OUT>
+ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, int64_t row_begin,
+                        int64_t row_end, void* ahi, void* alo, const int* moves, size_t smem,
+                        cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(trsm_kernel<T, kPanel / 32, OUT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return LD_ERR_CUDA;
+    attr = true;
+  }
   const int64_t rows = row_end - row_begin;
-  if (rows <= 0) return LD_OK;
-  const int warps = 8;
-  const int grid = (int)std::min<int64_t>(ceil_div(rows, warps), device_sm_count() * 2);
   ProfScope ps("trsm", stream, 3.0 * sizeof(T) * (double)rows * bb, (double)rows * bb * bb);
-  trsm_kernel<T, kPanel / 32><<<grid, 256, smem, stream>>>(F, ldf, (int)row_end, (int)s0, (int)bb,
-                                                          (int)m0, (int)row_begin, Cn, moves);
+  trsm_kernel<T, kPanel / 32, OUT><<<(unsigned)ceil_div(rows, 8), 256, smem, stream>>>(
+      F, ldf, (int)row_end, (int)s0, (int)bb, (int)m0, (int)row_begin, ahi, alo, moves);
   return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
 
-// Trailing update D[M x ncols] -= C[M x bb] R^T for the rows of one stream: the
-// tensor-core modes take B already in their format (ob), the FP64 mode Rt itself.
+// Multipliers of rows [row_begin, row_end) into the A operand rows [0, ...) at a.
 template <typename T>
-ld_status trailing_update(ld_mode mode, int64_t M, int64_t ncols, int64_t bb, const T* C,
-                          const T* Rt, const TcOperand& ob, void* a_scratch, T* D, int64_t ldd,
-                          int* err, cudaStream_t stream) {
+ld_status launch_trsm(ld_mode mode, T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0,
+                      int64_t row_begin, int64_t row_end, const OpBuf& a, const int* moves,
+                      cudaStream_t stream) {
+  if (row_end <= row_begin) return LD_OK;
+  const size_t smem = (size_t)bb * bb * sizeof(T);
+  if constexpr (sizeof(T) == 8) {
+    return launch_trsm_t<T, kOutT>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo, moves, smem,
+                                   stream);
+  } else {
+    switch (mode) {
+      case LD_F32_TF32:
+        return launch_trsm_t<T, kOutTF32>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo, moves,
+                                          smem, stream);
+      case LD_F32_3XTF32:
+        return launch_trsm_t<T, kOutTF32x3>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo,
+                                            moves, smem, stream);
+      case LD_F32_BF16X3:
+        return launch_trsm_t<T, kOutBF16x3>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo,
+                                            moves, smem, stream);
+      default:
+        return LD_ERR_INVALID_ARG;
+    }
+  }
+}
+
+// The panel rows transposed into the B operand (ncols rows of bb).
+template <typename T>
+ld_status launch_transpose(ld_mode mode, const T* F, int64_t ldf, int64_t s0, int64_t bb,
+                           int64_t ncols, const OpBuf& bo, cudaStream_t stream) {
+  dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(bb, 32));
+  ProfScope ps("transpose", stream, (sizeof(T) + (op_split(mode) ? 2.0 : 1.0) * bo.es) * ncols * bb,
+               0.0);
+  if constexpr (sizeof(T) == 8) {
+    transpose_rows_kernel<T, kOutT><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb, (int)ncols,
+                                                              bo.hi, bo.lo);
+  } else {
+    if (mode == LD_F32_TF32)
+      transpose_rows_kernel<T, kOutTF32><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
+                                                                   (int)ncols, bo.hi, bo.lo);
+    else if (mode == LD_F32_3XTF32)
+      transpose_rows_kernel<T, kOutTF32x3><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
+                                                                     (int)ncols, bo.hi, bo.lo);
+    else
+      transpose_rows_kernel<T, kOutBF16x3><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
+                                                                     (int)ncols, bo.hi, bo.lo);
+  }
+  return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
+}
+
+// Trailing update D[M x ncols] -= A B^T with the operands already in the mode's
+// format: rows [r0, r0 + M) of the A buffer, the whole B buffer.
+template <typename T>
+ld_status trailing_update(ld_mode mode, int64_t M, int64_t ncols, int64_t bb, const OpBuf& a,
+                          int64_t r0, const OpBuf& bo, T* D, int64_t ldd, int* err,
+                          cudaStream_t stream) {
   if (M <= 0 || ncols <= 0) return LD_OK;
+  const size_t off = (size_t)r0 * bb * a.es;
   if (mode == LD_F64_BLOCKED)
-    return rankb_update(mode, M, ncols, bb, C, bb, Rt, bb, D, ldd, nullptr, err, stream);
-  TcOperand oa;
-  ld_status st = rankb_prepare(mode, M, bb, reinterpret_cast<const float*>(C), bb, a_scratch, &oa,
-                               stream);
-  if (st != LD_OK) return st;
+    return rankb_update(mode, M, ncols, bb, a.hi + off, bb, bo.hi, bb, D, ldd, nullptr, err, stream);
+  const TcOperand oa{a.hi + off, a.lo ? a.lo + off : nullptr, bb, 0};
+  const TcOperand ob{bo.hi, bo.lo, bb, 0};
   return rankb_tc(mode, oa, ob, (int)M, (int)ncols, (int)bb, reinterpret_cast<float*>(D), ldd, 0, 1,
                   err, stream);
 }
@@ -200,31 +306,27 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   ld_status st = launch_stage<T>(A, a_dtype, lda, r, stream);
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);
-  const size_t cn_bytes = align_up((size_t)n * b * es, kAlign);
   const size_t grid_panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
   const size_t cl_bytes = align_up(panel_cluster_scratch_bytes(), kAlign);
-  const size_t bsc_bytes = align_up(rankb_operand_bytes(r.mode, n, b), kAlign);
-  const size_t anext_bytes = align_up(rankb_operand_bytes(r.mode, b, b), kAlign);
-  const size_t arest_bytes = bsc_bytes;
-  const size_t scratch_bytes = 3 * cn_bytes + grid_panel_bytes + 2 * cl_bytes + 2 * bsc_bytes +
-                               anext_bytes + arest_bytes + 2 * kAlign;
+  const size_t opb = op_bytes(r.mode, n, b);
+  // A and B operands double-buffered by panel parity: the low-priority stream
+  // may still read step k's while the critical stream writes step k+1's
+  const size_t scratch_bytes = grid_panel_bytes + 2 * cl_bytes + 4 * opb + 2 * kAlign;
   void* scratch = nullptr;
   st = scratch_alloc(&scratch, scratch_bytes, stream);
   if (st != LD_OK) return st;
   char* p = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
-  T* Cn[2] = {reinterpret_cast<T*>(p), reinterpret_cast<T*>(p + cn_bytes)};
-  p += 2 * cn_bytes;
-  T* Rt = reinterpret_cast<T*>(p);
-  p += cn_bytes;
   void* panel_scratch = p;
   p += grid_panel_bytes;
   char* cl_scratch[2] = {p, p + cl_bytes};
   p += 2 * cl_bytes;
-  char* bsc[2] = {p, p + bsc_bytes};
-  p += 2 * bsc_bytes;
-  char* anext = p;
-  p += anext_bytes;
-  char* arest = p;
+  OpBuf abuf[2], bbuf[2];
+  for (int q = 0; q < 2; ++q) {
+    abuf[q] = op_buf(r.mode, p, n, b);
+    p += opb;
+    bbuf[q] = op_buf(r.mode, p, n, b);
+    p += opb;
+  }
   // offset of the move list in the cluster panel's scratch
   const size_t moves_off = align_up((size_t)128 * 16 * 4, kAlign);
   // LD_PANEL=grid selects the grid-wide panel kernel instead of the cluster one
@@ -236,17 +338,6 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   const bool per_pivot = pp && pp[0] == '1';
   T* F = static_cast<T*>(r.F);
   int* err = &r.state->flags;
-  const size_t trsm_smem = (size_t)b * b * es;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[es == 8]) {
-    if (cudaFuncSetAttribute(trsm_kernel<T, kPanel / 32>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)trsm_smem) != cudaSuccess) {
-      scratch_free(scratch, stream);
-      return LD_ERR_CUDA;
-    }
-    attr_done[es == 8] = true;
-  }
   // streams and events of the pipeline (everything on the caller's stream when
   // they cannot be had)
   SweepStreams ss;
@@ -310,37 +401,26 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
       if (st != LD_OK) break;
     }
     const int* mv = used_cluster ? moves : nullptr;
-    st = launch_trsm<T>(F, r.ldf, s0, bb, m0, s0 + bb, s0 + bb + nb, Cn[par], mv, trsm_smem, hi);
+    st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb, s0 + bb + nb, abuf[par], mv, hi);
+    if (st == LD_OK) st = launch_transpose<T>(r.mode, F, r.ldf, s0, bb, ncols, bbuf[par], hi);
     if (st != LD_OK) break;
-    {
-      dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(bb, 32));
-      ProfScope ps("transpose", hi, 2.0 * es * (double)ncols * bb, 0.0);
-      transpose_rows_kernel<T><<<grid, 256, 0, hi>>>(F, r.ldf, (int)s0, (int)bb, (int)ncols, Rt);
-      if (cudaGetLastError() != cudaSuccess) {
-        st = LD_ERR_CUDA;
-        break;
-      }
-    }
-    TcOperand ob{nullptr, nullptr, bb, 0};
-    if (r.mode != LD_F64_BLOCKED) {
-      st = rankb_prepare(r.mode, ncols, bb, reinterpret_cast<const float*>(Rt), bb, bsc[par], &ob, hi);
-      if (st != LD_OK) break;
-    }
     // the remaining rows on lo: moves, multipliers and update, overlapping the
-    // next panel (they need this panel's moves, Rt and B, all on hi by now)
+    // next panel (they need this panel's moves and B, both on hi by now)
     if (rest > 0) {
+      OpBuf arest = abuf[par];
+      arest.hi += (size_t)nb * bb * arest.es;
+      if (arest.lo) arest.lo += (size_t)nb * bb * arest.es;
       st = link(hi, lo, ev[1]);
       if (st == LD_OK)
-        st = launch_trsm<T>(F, r.ldf, s0, bb, m0, s0 + bb + nb, n, Cn[par] + nb * bb, mv,
-                            trsm_smem, lo);
+        st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb + nb, n, arest, mv, lo);
       if (st == LD_OK)
-        st = trailing_update<T>(r.mode, rest, ncols, bb, Cn[par] + nb * bb, Rt, ob, arest,
+        st = trailing_update<T>(r.mode, rest, ncols, bb, abuf[par], nb, bbuf[par],
                                 F + (s0 + bb + nb) * r.ldf, r.ldf, err, lo);
       if (st != LD_OK) break;
       rest_pending = true;
     }
     // the next panel's rows on hi
-    st = trailing_update<T>(r.mode, nb, ncols, bb, Cn[par], Rt, ob, anext, F + (s0 + bb) * r.ldf,
+    st = trailing_update<T>(r.mode, nb, ncols, bb, abuf[par], 0, bbuf[par], F + (s0 + bb) * r.ldf,
                             r.ldf, err, hi);
   }
   // join every stream back into the caller's stream

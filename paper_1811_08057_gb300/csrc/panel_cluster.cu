@@ -501,7 +501,9 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(kCT);
-    cfg.dynamicSmemBytes = smem;
+    // at least 170 KB: no other kernel's CTA (the concurrent trailing update and
+    // multiplier kernels need 64 KB or more) shares an SM with the panel
+    cfg.dynamicSmemBytes = std::max<size_t>(smem, 170 * 1024);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
