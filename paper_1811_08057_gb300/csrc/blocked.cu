@@ -54,51 +54,88 @@ __device__ __forceinline__ void put_operand(void* hi, void* lo, int64_t idx, T x
   }
 }
 
-// Forward substitution for the multipliers of rows [row_begin, row_end): one
-// warp per row, lane L holding the values of pivots L, L+32, ... in registers.
-// The multipliers go to F (the factor record) and, as the update's A operand
-// (row i at (i - row_begin) * bb), to ahi / alo in format OUT. One row per warp
-// and short-lived CTAs, so a concurrent critical-path kernel finds free SMs.
+// Forward substitution for the multipliers of rows [row_begin, row_end): each
+// warp takes two rows and runs their substitutions interleaved, lane L holding
+// the values of pivots L, L+32, ... in registers. The multipliers go to F (the
+// factor record) and, as the update's A operand (row i at (i - row_begin) * bb),
+// to ahi / alo in format OUT. Short-lived CTAs (16 rows each), so a concurrent
+// critical-path kernel finds free SMs.
+constexpr int kTrsmRowsPerWarp = 2;
+constexpr int kTrsmRowsPerCta = 8 * kTrsmRowsPerWarp;
+
 template <typename T, int KMAX, int OUT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     trsm_kernel(T* __restrict__ F, int64_t ldf, int row_end, int s0, int bb, int m0, int row_begin,
                 void* __restrict__ ahi, void* __restrict__ alo, const int* __restrict__ moves) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* U = reinterpret_cast<T*>(smem_raw);  // bb x bb, U[t' * bb + t]
-  // U[t'][t] = factored row t' at the column of pivot t (t' < t), zero elsewhere
-  const int tot = bb * bb;
-#pragma unroll 16
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int tp = e / bb, t = e - tp * bb;
-    U[e] = (tp < t) ? F[(int64_t)(s0 + tp) * ldf + (m0 - 1 - t)] : T(0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // U[t'][t] = factored row t' at the column of pivot t (t' < t), zero elsewhere:
+  // one warp per row t', lanes over t
+  // (8 rows per warp at a time: their 8 x KMAX loads in flight together)
+  for (int r0 = 0; r0 < 32 * KMAX / 8; r0 += 8) {
+    T v[8][KMAX];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int tp = warp + 8 * (r0 + q);
+      const T* src = F + (int64_t)(s0 + tp) * ldf + (m0 - 1);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int t = lane + 32 * k;
+        v[q][k] = (tp < bb && tp < t && t < bb) ? src[-t] : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int tp = warp + 8 * (r0 + q);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int t = lane + 32 * k;
+        if (tp < bb && t < bb) U[tp * bb + t] = v[q][k];
+      }
+    }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int i = row_begin + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= row_end) return;
-  T* row = F + (int64_t)i * ldf;
+  const int i0 = row_begin + blockIdx.x * kTrsmRowsPerCta + warp * kTrsmRowsPerWarp;
+  if (i0 >= row_end) return;
+  const bool two = i0 + 1 < row_end;
+  T* row0 = F + (int64_t)i0 * ldf;
+  T* row1 = two ? row0 + ldf : row0;
   if (moves) {
-    // the panel's column exchanges, composed (moves[0] pairs of (dst, src))
+    // the panel's column exchanges, composed (moves[0] pairs of (dst, src)),
+    // both rows' gathers in flight together
     const int nm = moves[0];
-    T v[8];
+    int src[8], dst[8];
+    T v0[8], v1[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = lane + 32 * q;
-      v[q] = (k < nm) ? row[moves[2 + 2 * k]] : T(0);
+      src[q] = (k < nm) ? moves[2 + 2 * k] : 0;
+      dst[q] = (k < nm) ? moves[1 + 2 * k] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = lane + 32 * q;
+      v0[q] = (k < nm) ? row0[src[q]] : T(0);
+      v1[q] = (k < nm) ? row1[src[q]] : T(0);
     }
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = lane + 32 * q;
-      if (k < nm) row[moves[1 + 2 * k]] = v[q];
+      if (k < nm) {
+        row0[dst[q]] = v0[q];
+        if (two) row1[dst[q]] = v1[q];
+      }
     }
     __syncwarp();
   }
-  T a[KMAX];
+  T a[KMAX], b[KMAX];
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     const int t = lane + 32 * k;
-    a[k] = (t < bb) ? row[m0 - 1 - t] : T(0);
+    a[k] = (t < bb) ? row0[m0 - 1 - t] : T(0);
+    b[k] = (t < bb) ? row1[m0 - 1 - t] : T(0);
   }
 #pragma unroll
   for (int kk = 0; kk < KMAX; ++kk) {
@@ -106,22 +143,31 @@ __global__ void __launch_bounds__(256)
       for (int tt = 0; tt < 32; ++tt) {
         const int t = kk * 32 + tt;
         if (t >= bb) break;
-        const T c = __shfl_sync(0xffffffffu, a[kk], tt);
+        const T ca = __shfl_sync(0xffffffffu, a[kk], tt);
+        const T cb = __shfl_sync(0xffffffffu, b[kk], tt);
 #pragma unroll
         for (int k = kk; k < KMAX; ++k) {
           const int t2 = lane + 32 * k;
-          if (t2 > t && t2 < bb) a[k] = fma_t(-c, U[t * bb + t2], a[k]);
+          if (t2 > t && t2 < bb) {
+            const T u = U[t * bb + t2];
+            a[k] = fma_t(-ca, u, a[k]);
+            b[k] = fma_t(-cb, u, b[k]);
+          }
         }
       }
     }
   }
-  const int64_t base = (int64_t)(i - row_begin) * bb;
+  const int64_t base = (int64_t)(i0 - row_begin) * bb;
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     const int t = lane + 32 * k;
     if (t < bb) {
-      row[m0 - 1 - t] = a[k];
+      row0[m0 - 1 - t] = a[k];
       put_operand<OUT, T>(ahi, alo, base + t, a[k]);
+      if (two) {
+        row1[m0 - 1 - t] = b[k];
+        put_operand<OUT, T>(ahi, alo, base + bb + t, b[k]);
+      }
     }
   }
 }
@@ -226,7 +272,7 @@ ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, i
   }
   const int64_t rows = row_end - row_begin;
   ProfScope ps("trsm", stream, 3.0 * sizeof(T) * (double)rows * bb, (double)rows * bb * bb);
-  trsm_kernel<T, kPanel / 32, OUT><<<(unsigned)ceil_div(rows, 8), 256, smem, stream>>>(
+  trsm_kernel<T, kPanel / 32, OUT><<<(unsigned)ceil_div(rows, kTrsmRowsPerCta), 256, smem, stream>>>(
       F, ldf, (int)row_end, (int)s0, (int)bb, (int)m0, (int)row_begin, ahi, alo, moves);
   return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
