@@ -373,8 +373,6 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     bbuf[q] = op_buf(r.mode, p, n, b);
     p += opb;
   }
-  // offset of the move list in the cluster panel's scratch
-  const size_t moves_off = align_up((size_t)128 * 16 * 4, kAlign);
   // LD_PANEL=grid selects the grid-wide panel kernel instead of the cluster one
   const char* pk = getenv("LD_PANEL");
   const bool no_cluster = pk && pk[0] == 'g';
@@ -403,7 +401,7 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
     const int par = (int)(k & 1);
-    const int* moves = reinterpret_cast<const int*>(cl_scratch[par] + moves_off);
+    const int* moves = reinterpret_cast<const int*>(cl_scratch[par]);  // the panel's move list
     bool used_cluster = false;
     ld_status pst = LD_ERR_UNSUPPORTED;
     if (!per_pivot && !no_cluster && sizeof(T) == 4) {

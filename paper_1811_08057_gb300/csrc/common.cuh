@@ -175,51 +175,53 @@ __device__ __forceinline__ void candf_warp_reduce(CandF& c) {
 // Keyed FP32 candidate for warp reductions with redux.sync, the same ordering as
 // CandF: key = bit pattern of |v| plus one (0 = no candidate; for non-NaN values
 // the order of |v| is the unsigned order of these patterns, and -0 and +0 share
-// one key), equal keys go to the smaller original label.
+// one key; a NaN takes the largest key), equal keys go to the smaller original
+// label. ps packs the position (bits 0-30) and the sign of v (bit 31).
+constexpr unsigned kKeyNaN = 0xffffffffu;
+
 struct KCand {
   unsigned key;
   int label;
-  int pos;
-  float v;
-  int nan;
+  unsigned ps;
 };
 
 __device__ __forceinline__ void kc_init(KCand& c) {
   c.key = 0u;
   c.label = 0x7fffffff;
-  c.pos = -1;
-  c.v = 0.f;
-  c.nan = 0;
+  c.ps = 0u;
 }
 
 __device__ __forceinline__ void kc_offer(KCand& c, float v, int label, int pos) {
-  const unsigned ab = __float_as_uint(v) & 0x7fffffffu;
-  if (ab > 0x7f800000u) {
-    c.nan = 1;
-    return;
-  }
-  const unsigned key = ab + 1u;
+  const unsigned bits = __float_as_uint(v);
+  const unsigned ab = bits & 0x7fffffffu;
+  const unsigned key = (ab > 0x7f800000u) ? kKeyNaN : ab + 1u;
   if (key > c.key || (key == c.key && label < c.label)) {
     c.key = key;
-    c.v = v;
     c.label = label;
-    c.pos = pos;
+    c.ps = (unsigned)pos | (bits & 0x80000000u);
   }
 }
 
+__device__ __forceinline__ int kc_pos(const KCand& c) { return (int)(c.ps & 0x7fffffffu); }
+__device__ __forceinline__ float kc_value(const KCand& c) {
+  return __uint_as_float((c.key - 1u) | (c.ps & 0x80000000u));
+}
+
 // Best candidate of the warp, delivered to every lane; returns the lane that
-// held it (any lane when no lane has a candidate).
+// held it (any lane when no lane has a candidate). The label tie-break runs only
+// when several lanes share the largest key.
 __device__ __forceinline__ int kc_warp_best(KCand& c) {
   const unsigned kmax = __reduce_max_sync(0xffffffffu, c.key);
-  const unsigned lab = (c.key == kmax) ? (unsigned)c.label : 0xffffffffu;
-  const unsigned lmin = __reduce_min_sync(0xffffffffu, lab);
-  const unsigned won = __ballot_sync(0xffffffffu, c.key == kmax && (unsigned)c.label == lmin);
+  unsigned won = __ballot_sync(0xffffffffu, c.key == kmax);
+  if ((won & (won - 1u)) != 0u && kmax != 0u && kmax != kKeyNaN) {
+    const unsigned lab = (c.key == kmax) ? (unsigned)c.label : 0xffffffffu;
+    const unsigned lmin = __reduce_min_sync(0xffffffffu, lab);
+    won = __ballot_sync(0xffffffffu, c.key == kmax && (unsigned)c.label == lmin);
+  }
   const int src = __ffs(won) - 1;
-  c.pos = __shfl_sync(0xffffffffu, c.pos, src);
-  c.v = __shfl_sync(0xffffffffu, c.v, src);
   c.key = kmax;
-  c.label = (int)lmin;
-  c.nan = __any_sync(0xffffffffu, c.nan);
+  c.label = __shfl_sync(0xffffffffu, c.label, src);
+  c.ps = __shfl_sync(0xffffffffu, c.ps, src);
   return src;
 }
 

@@ -59,7 +59,6 @@ struct ClusterArgs {
   int* pivpos;
   double* pivval;
   SweepState* st;
-  float* crow;      // [kBMax][kKI] multipliers of the rows below the inner block
   int* moves;       // [1 + 2 * 2 * kBMax]: count, then (dst, src) position pairs
   int* dlist;       // [1 + 3 * 2 * kBMax]: count, then (position, new label, old label)
   int logsum;       // 1: accumulate the panel's sign and log-sum here; 0: the caller does
@@ -143,22 +142,21 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         kc_init(cb);
       kc_warp_best(cb);  // every warp holds the CTA's candidate
       // push candidate, its column and the boundary column to every CTA (a fixed
-      // byte count: absent values are sent as zeros; a NaN in the CTA's
-      // positions is sent as the largest key)
+      // byte count: absent values are sent as zeros)
       const bool own_last = (m - 1 >= j_lo) && (m - 1 < j_hi);
       const uint32_t bar_l = tc::smem_u32(&xbar[par]);
       for (int e = tid; e < CL * kKI; e += kCT) {
         const int d = e / kKI, i = e % kKI;
         const uint32_t rbar = tc::mapa(bar_l, d);
-        const float cv = (i < kb && cb.pos >= 0) ? S[i * W + (cb.pos - j_lo)] : 0.f;
+        const float cv = (i < kb && cb.key != 0u) ? S[i * W + (kc_pos(cb) - j_lo)] : 0.f;
         tc::st_async_b32(tc::mapa(tc::smem_u32(&pcand[par][c][i]), d), __float_as_uint(cv), rbar);
         if (own_last) {
           const float lv = (i < kb) ? S[i * W + (m - 1 - j_lo)] : 0.f;
           tc::st_async_b32(tc::mapa(tc::smem_u32(&plast[par][i]), d), __float_as_uint(lv), rbar);
         }
         if (i == 0) {
-          tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), cb.nan ? 0xffffffffu : cb.key,
-                          (uint32_t)cb.label, (uint32_t)cb.pos, __float_as_uint(cb.v), rbar);
+          tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), cb.key, (uint32_t)cb.label,
+                          cb.ps, 0u, rbar);
           if (own_last)
             tc::st_async_b32(tc::mapa(tc::smem_u32(&plastlab[par]), d), (uint32_t)lab[m - 1 - j_lo],
                              rbar);
@@ -175,22 +173,19 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         const uint4 q = pslot[par][lane];
         g.key = q.x;
         g.label = (int)q.y;
-        g.pos = (int)q.z;
-        g.v = __uint_as_float(q.w);
-        g.nan = (q.x == 0xffffffffu);
-        if (g.nan) g.key = 0u;
+        g.ps = q.z;
       } else {
         kc_init(g);
       }
       const int wc = kc_warp_best(g);  // the winning CTA (identical in every warp)
-      const bool ok = !g.nan && g.key > 1u;
+      const bool ok = g.key != kKeyNaN && g.key > 1u;
       if (!ok) {
-        if (c == 0 && tid == 0) atomicOr(&a.st->flags, g.nan ? kFlagNaN : kFlagSingular);
+        if (c == 0 && tid == 0) atomicOr(&a.st->flags, g.key == kKeyNaN ? kFlagNaN : kFlagSingular);
         bad = 1;
         break;
       }
-      const int l = g.pos;
-      const float pf = g.v;
+      const int l = kc_pos(g);
+      const float pf = kc_value(g);
       if (tid == 0) s_swap[t] = l;
       if (c == 0 && tid == 0) {  // the sign and the log-sum are accumulated after the panel
         a.pivpos[row0 + t] = l;
@@ -253,9 +248,18 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     }
     // after a failed pivot or a timeout the CTAs only keep the barrier sequence
     // the inner block is final: back to F (own positions)
-    if (!bad)
-      for (int t = 0; t < kb; ++t)
-        for (int j = tid; j < w_own; j += kCT) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
+    if (!bad) {
+#pragma unroll
+      for (int t = 0; t < kKI; ++t) {
+        if (t < kb) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int j = tid + k * kCT;
+            if (j < w_own) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
+          }
+        }
+      }
+    }
     // composed column moves of this block (every CTA computes the same list):
     // lane k of warp 0 takes one position the block's exchanges touched (lanes
     // k < kb: l_k, lanes kb + k: mq-1-k; one representative per distinct
@@ -321,13 +325,10 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         }
         if (lane < kb) {
           row[mq - 1 - lane] = x;  // multipliers (L) of this block
-          a.crow[r * kKI + lane] = x;
+          for (int d = 0; d < CL; ++d) cluster.map_shared_rank(Cm, d)[r * kKI + lane] = x;
         }
       }
-      cluster.sync();  // multipliers and moved values visible to every CTA
-      for (int e = tid; e < rows_below * kKI && !bad; e += kCT)
-        Cm[e] = (e % kKI < kb) ? __ldcg(a.crow + e) : 0.f;
-      __syncthreads();
+      cluster.sync();  // multipliers (in every CTA's Cm) and moved values visible
       // (b) the block's rank-1 updates on the own positions, in pivot order:
       // register tiles of kRU rows x 2 positions, their loads in flight together
       const int wq = bad ? 0 : max(0, min(j_hi, mq - kb) - j_lo);
@@ -465,8 +466,7 @@ __global__ void apply_moves_kernel(float* __restrict__ F, int64_t ldf, int r0, i
 }  // namespace
 
 size_t panel_cluster_scratch_bytes() {
-  return align_up((size_t)kBMax * kKI * 4, kAlign) + align_up((1 + 4 * kBMax) * 4, kAlign) +
-         align_up((1 + 6 * kBMax) * 4, kAlign);
+  return align_up((1 + 4 * kBMax) * 4, kAlign) + align_up((1 + 6 * kBMax) * 4, kAlign);
 }
 
 // Launches the cluster panel for rows [s0, s0+bb) and, for the rows outside the
@@ -517,14 +517,11 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
       cudaGetLastError();
       continue;
     }
-    char* p = static_cast<char*>(scratch);
-    float* crow = reinterpret_cast<float*>(p);
-    int* moves = reinterpret_cast<int*>(p + align_up((size_t)kBMax * kKI * 4, kAlign));
-    int* dlist = reinterpret_cast<int*>(p + align_up((size_t)kBMax * kKI * 4, kAlign) +
+    int* moves = static_cast<int*>(scratch);  // at offset 0: see the header
+    int* dlist = reinterpret_cast<int*>(static_cast<char*>(scratch) +
                                         align_up((1 + 4 * kBMax) * 4, kAlign));
     ClusterArgs a{static_cast<float*>(r.F), r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
-                  r.colperm, r.pivpos, r.pivval, r.state, crow, moves, dlist,
-                  defer_logsum ? 0 : 1};
+                  r.colperm, r.pivpos, r.pivval, r.state, moves, dlist, defer_logsum ? 0 : 1};
     cudaError_t e;
     {
       ProfScope ps("panel", stream, 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),

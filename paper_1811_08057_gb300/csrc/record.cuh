@@ -155,6 +155,8 @@ ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row
                        void* scratch, cudaStream_t stream);
 
 // ---- cluster panel kernel (panel_cluster.cu), FP32 storage ----
+// Scratch of one launch; it starts with the panel's composed column moves for
+// the rows outside the panel: int count, then count (dst, src) position pairs.
 size_t panel_cluster_scratch_bytes();
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
                                void* scratch, bool defer_logsum, cudaStream_t stream);
