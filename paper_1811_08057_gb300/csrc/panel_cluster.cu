@@ -64,7 +64,8 @@ struct ClusterArgs {
   int logsum;       // 1: accumulate the panel's sign and log-sum here; 0: the caller does
 };
 
-// K: positions per thread (W <= K * kCT).
+// K: positions per thread (W <= K * kCT). The thread's values of the inner
+// block live in registers: x[i][k] = row i at position c*W + tid + k*kCT.
 template <int K>
 __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -76,8 +77,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   const int w_own = max(0, j_hi - j_lo);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* S = reinterpret_cast<float*>(smem_raw);          // kKI x W slice of the inner block
-  float* U = S + (size_t)kKI * W;                         // kKI x kKI (block's U)
+  float* U = reinterpret_cast<float*>(smem_raw);          // kKI x kKI (block's U)
   float* Cm = U + kKI * kKI;                              // kBMax x kKI multipliers below
   int* lab = reinterpret_cast<int*>(Cm + kBMax * kKI);    // W labels
   __shared__ __align__(16) uint4 pslot[2][kCLMax];  // candidates pushed by every CTA
@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   __shared__ int plastlab[2];
   __shared__ __align__(8) uint64_t xbar[2];         // bytes received per pivot parity
   __shared__ KCand wred[2][kCT / 32];
+  __shared__ float wcol[2][kCT / 32][kKI];          // each warp's candidate column
+  __shared__ float lcol[2][kKI];                    // this CTA's boundary column, if owned
   __shared__ int s_nmoved;
   __shared__ int s_swap[kKI];
   __shared__ int mv_dst[2 * kKI], mv_src[2 * kKI];
@@ -110,15 +112,23 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   const uint32_t xbytes = (uint32_t)CL * (16u + 4u * kKI) + 4u * kKI + 4u;
   cluster.sync();  // every mbarrier initialised before the first push
 
+  float x[kKI][K];  // the inner block at the own positions
   for (int q0 = 0; q0 < bb; q0 += kKI) {
     const int kb = min(kKI, bb - q0);
     const int mq = m0 - q0;  // active columns at the start of this inner block
     const int64_t row0 = (int64_t)(a.s0 + q0);
-    // inner block rows into the slice, own positions (other CTAs wrote some of
-    // these values: read past L1)
-    if (!bad)
-      for (int t = 0; t < kb; ++t)
-        for (int j = tid; j < w_own; j += kCT) S[t * W + j] = __ldcg(F + (row0 + t) * a.ldf + j_lo + j);
+    // inner block rows into registers (other CTAs wrote some of these values:
+    // read past L1)
+#pragma unroll
+    for (int i = 0; i < kKI; ++i)
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int j = tid + k * kCT;
+        x[i][k] = (!bad && i < kb && j < w_own) ? __ldcg(F + (row0 + i) * a.ldf + j_lo + j) : 0.f;
+      }
+    float cur[K];  // the current pivot row at the own positions
+#pragma unroll
+    for (int k = 0; k < K; ++k) cur[k] = x[0][k];
     for (int t = 0; t < kb && !bad; ++t) {
       const int m = mq - t;
       const int gi = q0 + t;  // pivot index in the panel
@@ -130,9 +140,28 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
-        if (j < w_act) kc_offer(cd, S[t * W + j], lab[j], j_lo + j);
+        if (j < w_act) kc_offer(cd, cur[k], lab[j], j_lo + j);
       }
-      kc_warp_best(cd);
+      const int src = kc_warp_best(cd);
+      // the warp's candidate column and (its owner) the boundary column, staged
+      // for the push
+      const int jc = kc_pos(cd) - j_lo;
+      if (lane == src && cd.key != 0u) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (tid + k * kCT == jc)
+#pragma unroll
+            for (int i = 0; i < kKI; ++i) wcol[par][warp][i] = x[i][k];
+      }
+      const int jm = m - 1 - j_lo;
+      const bool own_last = (jm >= 0) && (jm < w_own);
+      if (own_last && jm % kCT == tid) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (tid + k * kCT == jm)
+#pragma unroll
+            for (int i = 0; i < kKI; ++i) lcol[par][i] = x[i][k];
+      }
       if (lane == 0) wred[par][warp] = cd;
       __syncthreads();
       KCand cb;
@@ -140,26 +169,24 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         cb = wred[par][lane];
       else
         kc_init(cb);
-      kc_warp_best(cb);  // every warp holds the CTA's candidate
+      const int wb = kc_warp_best(cb);  // every warp holds the CTA's candidate
       // push candidate, its column and the boundary column to every CTA (a fixed
       // byte count: absent values are sent as zeros)
-      const bool own_last = (m - 1 >= j_lo) && (m - 1 < j_hi);
       const uint32_t bar_l = tc::smem_u32(&xbar[par]);
       for (int e = tid; e < CL * kKI; e += kCT) {
         const int d = e / kKI, i = e % kKI;
         const uint32_t rbar = tc::mapa(bar_l, d);
-        const float cv = (i < kb && cb.key != 0u) ? S[i * W + (kc_pos(cb) - j_lo)] : 0.f;
+        const float cv = (i < kb && cb.key != 0u) ? wcol[par][wb][i] : 0.f;
         tc::st_async_b32(tc::mapa(tc::smem_u32(&pcand[par][c][i]), d), __float_as_uint(cv), rbar);
         if (own_last) {
-          const float lv = (i < kb) ? S[i * W + (m - 1 - j_lo)] : 0.f;
+          const float lv = (i < kb) ? lcol[par][i] : 0.f;
           tc::st_async_b32(tc::mapa(tc::smem_u32(&plast[par][i]), d), __float_as_uint(lv), rbar);
         }
         if (i == 0) {
           tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), cb.key, (uint32_t)cb.label,
                           cb.ps, 0u, rbar);
           if (own_last)
-            tc::st_async_b32(tc::mapa(tc::smem_u32(&plastlab[par]), d), (uint32_t)lab[m - 1 - j_lo],
-                             rbar);
+            tc::st_async_b32(tc::mapa(tc::smem_u32(&plastlab[par]), d), (uint32_t)lab[jm], rbar);
         }
       }
       if (tid == 0) tc::mbar_arrive_expect_tx(&xbar[par], xbytes);
@@ -193,56 +220,42 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       }
       const float* pc = pcand[par][wc];  // pivot column: the multipliers of the block's rows
       const float* lc = plast[par];      // boundary column
-      const int jl = l - j_lo, jm = m - 1 - j_lo;
+      const int jl = l - j_lo;
+      float pcv[kKI];
+#pragma unroll
+      for (int i = 0; i < kKI; ++i) pcv[i] = pc[i];
       if (l != m - 1) {
-        // the warp of each owner writes the exchanged column, one row per lane
-        if (jl >= 0 && jl < w_own && (jl % kCT) / 32 == warp) {
-          if (lane < kb && lane != t) S[lane * W + jl] = lc[lane];
-          if (jl % kCT == tid) lab[jl] = plastlab[par];
+        // exchange of columns l and m-1 (Sec. 2.4), by their owners
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int j = tid + k * kCT;
+          if (j == jl) {
+#pragma unroll
+            for (int i = 0; i < kKI; ++i)
+              if (i != t) x[i][k] = lc[i];
+            lab[jl] = plastlab[par];
+          }
+          if (j == jm) {
+#pragma unroll
+            for (int i = 0; i < kKI; ++i) x[i][k] = pcv[i];
+            lab[jm] = g.label;
+          }
         }
-        if (jm >= 0 && jm < w_own && (jm % kCT) / 32 == warp) {
-          if (lane < kb) S[lane * W + jm] = pc[lane];
-          if (jm % kCT == tid) lab[jm] = g.label;
-        }
-        __syncwarp();
       }
       // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
       // then the rank-1 update of the block's later rows, position by position
       const int jend = min(w_own, m - 1 - j_lo);
-      float r[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
-        r[k] = 0.f;
         if (j < jend) {
-          const float v = (j == jl) ? lc[t] : S[t * W + j];
-          r[k] = __fdiv_rn(v, pf);
-          S[t * W + j] = r[k];
-        }
-      }
-      // four rows at a time: their loads in flight together
-      int i = t + 1;
-      for (; i + 3 < kb; i += 4) {
-        const float c0 = pc[i], c1 = pc[i + 1], c2 = pc[i + 2], c3 = pc[i + 3];
+          const float r = __fdiv_rn((j == jl) ? lc[t] : cur[k], pf);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int j = tid + k * kCT;
-          if (j < jend) {
-            float* col = S + (size_t)i * W + j;
-            const float a0 = col[0], a1 = col[W], a2 = col[2 * W], a3 = col[3 * W];
-            col[0] = fmaf(-c0, r[k], a0);
-            col[W] = fmaf(-c1, r[k], a1);
-            col[2 * W] = fmaf(-c2, r[k], a2);
-            col[3 * W] = fmaf(-c3, r[k], a3);
+          for (int i = 0; i < kKI; ++i) {
+            if (i == t) x[i][k] = r;
+            if (i > t && i < kb) x[i][k] = fmaf(-pcv[i], r, x[i][k]);
+            if (i == t + 1) cur[k] = x[i][k];
           }
-        }
-      }
-      for (; i < kb; ++i) {
-        const float ci = pc[i];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int j = tid + k * kCT;
-          if (j < jend) S[i * W + j] = fmaf(-ci, r[k], S[i * W + j]);
         }
       }
     }
@@ -250,12 +263,12 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     // the inner block is final: back to F (own positions)
     if (!bad) {
 #pragma unroll
-      for (int t = 0; t < kKI; ++t) {
-        if (t < kb) {
+      for (int i = 0; i < kKI; ++i) {
+        if (i < kb) {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const int j = tid + k * kCT;
-            if (j < w_own) F[(row0 + t) * a.ldf + j_lo + j] = S[t * W + j];
+            if (j < w_own) F[(row0 + i) * a.ldf + j_lo + j] = x[i][k];
           }
         }
       }
@@ -334,14 +347,17 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       const int wq = bad ? 0 : max(0, min(j_hi, mq - kb) - j_lo);
       const float4* Cm4 = reinterpret_cast<const float4*>(Cm);
       float* base = F + (row0 + kb) * a.ldf + j_lo;
-      for (int j0 = tid; j0 < wq; j0 += 2 * kCT) {
+#pragma unroll
+      for (int kp = 0; kp < K; kp += 2) {
+        const int j0 = tid + kp * kCT;
+        if (j0 >= wq) break;
         const int j1 = j0 + kCT;
-        const bool has1 = j1 < wq;
+        const bool has1 = kp + 1 < K && j1 < wq;
         float s0v[kKI], s1v[kKI];
 #pragma unroll
         for (int t = 0; t < kKI; ++t) {
-          s0v[t] = (t < kb) ? S[t * W + j0] : 0.f;
-          s1v[t] = (t < kb && has1) ? S[t * W + j1] : 0.f;
+          s0v[t] = x[t][kp];
+          s1v[t] = has1 ? x[t][kp + 1 < K ? kp + 1 : kp] : 0.f;
         }
         // the next chunk's loads are issued before this chunk's FMAs
         float n0[kRU], n1[kRU];
@@ -487,8 +503,7 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     const int CL = sizes[si];
     if (cl_ok > 0 && CL != cl_ok) continue;
     const int64_t W = ceil_div(m0, CL);
-    const size_t smem = (size_t)kKI * W * 4 + kKI * kKI * 4 + (size_t)kBMax * kKI * 4 +
-                        (size_t)W * 4;
+    const size_t smem = kKI * kKI * 4 + (size_t)kBMax * kKI * 4 + (size_t)W * 4;
     if (smem > 200 * 1024 || W > 8 * kCT) continue;
     const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
     void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<1>
