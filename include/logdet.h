@@ -123,8 +123,14 @@ ld_status ld_logdet_backward(const void* factors, const double* g, void* grad, i
  *   n_max    host bound on every n[i] (sizes the workspace); n[i] > n_max gives
  *            NaN for that matrix
  *   signs, logabs  device arrays of `count` doubles
- * Modes: LD_F32_PLAIN and LD_F64_PLAIN. No host synchronisation; the call can
- * be captured in a CUDA graph once its workspace exists (see ld_batched_reserve).
+ * Modes: LD_F32_PLAIN and LD_F64_PLAIN (one persistent launch, any mix of
+ * sizes), and LD_F32_TF32 / LD_F32_3XTF32 / LD_F32_BF16X3 for a batch of one size
+ * n_max (n[i] = n_max for every i; another size gives NaN for that matrix): the
+ * blocked sweep of ld_logdet run panel by panel across the whole batch (a
+ * one-CTA panel kernel per matrix, then batched multipliers and one batched
+ * tensor-core rank-b update per panel), n_max <= 2048 and count <= 65535. No
+ * host synchronisation; the call can be captured in a CUDA graph once its
+ * workspace exists.
  */
 ld_status ld_logdet_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                             const int64_t* lda, int64_t count, int64_t n_max, ld_mode mode,

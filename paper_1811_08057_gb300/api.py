@@ -141,7 +141,9 @@ class BatchedInputs:
 
 def logdet_batched(batch, mode="f32_plain", stream=None, out=None):
     """sign and log|det| of every matrix of a batch (list of CUDA tensors or a
-    BatchedInputs) in one persistent launch. Returns (signs, logabs) FP64 tensors."""
+    BatchedInputs). f64_plain / f32_plain: one persistent launch, any sizes; the
+    FP32 tensor-core modes: a batch of one size, blocked panel by panel across the
+    batch. Returns (signs, logabs) FP64 tensors."""
     if not isinstance(batch, BatchedInputs):
         batch = BatchedInputs(batch)
     if out is None:
@@ -198,8 +200,9 @@ class LogAbsDet(torch.autograd.Function):
         n = A.shape[-1]
         dev = A.device
         if batched:
-            if mode_c not in (_lib.LD_F64_PLAIN, _lib.LD_F32_PLAIN):
-                raise ValueError("batched forward supports f64_plain / f32_plain")
+            if mode_c == _lib.LD_F64_BLOCKED:
+                raise ValueError("batched forward supports f64_plain, f32_plain and the FP32 "
+                                 "tensor-core modes")
             mats = [M.contiguous() for M in mats]
             batch = BatchedInputs(mats)
             buf, offs = _aligned_records([n] * len(mats), mode_c, dev)

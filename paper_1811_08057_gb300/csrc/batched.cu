@@ -448,10 +448,14 @@ static ld_status batched_entry(const void* const* A_ptrs, ld_dtype a_dtype, cons
   if (count < 0 || n_max < 0 || (count > 0 && (!A_ptrs || !n || !lda || !signs || !logabs)))
     return LD_ERR_INVALID_ARG;
   if (a_dtype != LD_DTYPE_F64 && a_dtype != LD_DTYPE_F32) return LD_ERR_INVALID_ARG;
-  if (mode != LD_F64_PLAIN && mode != LD_F32_PLAIN) return mode_valid(mode) ? LD_ERR_UNSUPPORTED : LD_ERR_INVALID_ARG;
+  if (!mode_valid(mode)) return LD_ERR_INVALID_ARG;
   if (count == 0) return LD_OK;
-  if (count > 0x7fffffff || n_max > 4096) return LD_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (mode == LD_F32_TF32 || mode == LD_F32_3XTF32 || mode == LD_F32_BF16X3)
+    return run_blocked_batched(A_ptrs, a_dtype, n, lda, count, n_max, mode, factors, signs, logabs,
+                               s);
+  if (mode != LD_F64_PLAIN && mode != LD_F32_PLAIN) return LD_ERR_UNSUPPORTED;
+  if (count > 0x7fffffff || n_max > 4096) return LD_ERR_UNSUPPORTED;
   if (mode == LD_F64_PLAIN)
     return run_batched<double>(A_ptrs, a_dtype, n, lda, count, std::max<int64_t>(n_max, 1), signs,
                                logabs, factors, mode, s);

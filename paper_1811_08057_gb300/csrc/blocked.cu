@@ -63,11 +63,22 @@ __device__ __forceinline__ void put_operand(void* hi, void* lo, int64_t idx, T x
 constexpr int kTrsmRowsPerWarp = 2;
 constexpr int kTrsmRowsPerCta = 8 * kTrsmRowsPerWarp;
 
+// Batched form (recs != nullptr): matrix blockIdx.z, F at recs[z] + f_off bytes,
+// its operand rows a_zs elements further per matrix, its moves mv_zs bytes.
 template <typename T, int KMAX, int OUT>
 __global__ void __launch_bounds__(256, 3)
     trsm_kernel(T* __restrict__ F, int64_t ldf, int row_end, int s0, int bb, int m0, int row_begin,
-                void* __restrict__ ahi, void* __restrict__ alo, const int* __restrict__ moves) {
+                void* __restrict__ ahi, void* __restrict__ alo, const int* __restrict__ moves,
+                void* const* __restrict__ recs, int64_t f_off, int64_t a_zs, int64_t mv_zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (recs) {
+    const int z = blockIdx.z;
+    F = reinterpret_cast<T*>(static_cast<char*>(recs[z]) + f_off);
+    const size_t es = (OUT == kOutBF16x3) ? 2 : sizeof(float) * (OUT == kOutT ? sizeof(T) / 4 : 1);
+    ahi = static_cast<char*>(ahi) + (size_t)z * a_zs * es;
+    if (alo) alo = static_cast<char*>(alo) + (size_t)z * a_zs * es;
+    if (moves) moves = reinterpret_cast<const int*>(reinterpret_cast<const char*>(moves) + z * mv_zs);
+  }
   T* U = reinterpret_cast<T*>(smem_raw);  // bb x bb, U[t' * bb + t]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // U[t'][t] = factored row t' at the column of pivot t (t' < t), zero elsewhere:
@@ -176,8 +187,16 @@ __global__ void __launch_bounds__(256, 3)
 // memory), written in format OUT: the update's B operand.
 template <typename T, int OUT>
 __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int s0, int bb,
-                                      int ncols, void* __restrict__ bhi, void* __restrict__ blo) {
+                                      int ncols, void* __restrict__ bhi, void* __restrict__ blo,
+                                      void* const* __restrict__ recs, int64_t f_off, int64_t b_zs) {
   __shared__ T tile[32][33];
+  if (recs) {
+    const int z = blockIdx.z;
+    F = reinterpret_cast<const T*>(static_cast<char*>(recs[z]) + f_off);
+    const size_t es = (OUT == kOutBF16x3) ? 2 : sizeof(float) * (OUT == kOutT ? sizeof(T) / 4 : 1);
+    bhi = static_cast<char*>(bhi) + (size_t)z * b_zs * es;
+    if (blo) blo = static_cast<char*>(blo) + (size_t)z * b_zs * es;
+  }
   const int j0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
   for (int k = ty; k < 32; k += 8) {
@@ -189,6 +208,85 @@ __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int 
     const int j = j0 + k, t = t0 + tx;
     if (j < ncols && t < bb) put_operand<OUT, T>(bhi, blo, (int64_t)j * bb + t, tile[tx][k]);
   }
+}
+
+// ------------------------------------------------------ batched blocked sweep
+// Stage of matrix blockIdx.z into its record (FP32 storage): F = A (any input
+// type and lda), colperm = identity, sweep state reset, header size fields. A
+// matrix whose n differs from the batch's is flagged (kFlagBadSize).
+__global__ void stage_batched_kernel(const void* const* __restrict__ A_ptrs, int a_dtype,
+                                     const int64_t* __restrict__ n_arr,
+                                     const int64_t* __restrict__ lda_arr, int n, int64_t ldf,
+                                     int mode, void* const* __restrict__ recs, RecOffsets ro) {
+  const int z = blockIdx.z;
+  char* b = static_cast<char*>(recs[z]);
+  SweepState* st = reinterpret_cast<SweepState*>(b + ro.state);
+  const bool size_ok = n_arr[z] == n;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    RecordHeader* h = reinterpret_cast<RecordHeader*>(b + ro.header);
+    h->n = n;
+    h->ldf = ldf;
+    h->mode = mode;
+    st->sign = 1.0;
+    st->sum = 0.0;
+    st->comp = 0.0;
+    st->flags = size_ok ? 0 : kFlagBadSize;
+    st->steps = 0;
+  }
+  if (!size_ok) return;
+  float* F = reinterpret_cast<float*>(b + ro.F);
+  const int64_t lda = lda_arr[z];
+  const void* A = A_ptrs[z];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const int64_t idx = (int64_t)i * lda + j;
+    F[(int64_t)i * ldf + j] = a_dtype == LD_DTYPE_F64 ? (float)static_cast<const double*>(A)[idx]
+                                                      : static_cast<const float*>(A)[idx];
+  }
+  if (blockIdx.y == 0) reinterpret_cast<int*>(b + ro.colperm)[j] = j;
+}
+
+// Sign, compensated log-sum (in pivot order, the same steps as per pivot) and
+// the result of every matrix: one warp per matrix.
+__global__ void finalize_batched_kernel(void* const* __restrict__ recs, RecOffsets ro, int n,
+                                        int count, const int* __restrict__ err,
+                                        double* __restrict__ signs, double* __restrict__ logabs) {
+  const int z = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (z >= count) return;
+  char* b = static_cast<char*>(recs[z]);
+  const SweepState* st = reinterpret_cast<const SweepState*>(b + ro.state);
+  const int flags = *reinterpret_cast<const volatile int*>(&st->flags) | *err;
+  double sign = 1.0, sum = 0.0, comp = 0.0;
+  if (flags == 0)
+    panel_sign_logsum(reinterpret_cast<const double*>(b + ro.pivval),
+                      reinterpret_cast<const int*>(b + ro.pivpos), 0, n, n, sign, sum, comp);
+  if (lane != 0) return;
+  double sg, la;
+  if (n == 0) {
+    sg = 1.0;
+    la = 0.0;
+  } else if (flags & (kFlagNaN | kFlagTimeout | kFlagBadSize)) {
+    sg = la = __longlong_as_double(0x7ff8000000000000ULL);
+  } else if (flags & kFlagSingular) {
+    sg = 0.0;
+    la = -__longlong_as_double(0x7ff0000000000000ULL);
+  } else {
+    sg = sign;
+    la = sum + comp;
+  }
+  RecordHeader* h = reinterpret_cast<RecordHeader*>(b + ro.header);
+  h->flags = flags;
+  h->sign = sg;
+  h->logabs = la;
+  signs[z] = sg;
+  logabs[z] = la;
+}
+
+__global__ void fill_ptrs_kernel(char* base, int64_t stride, int count, void** out) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < count) out[z] = base + (int64_t)z * stride;
 }
 
 // Streams of one device for the look-ahead pipeline of the blocked sweep:
@@ -238,6 +336,15 @@ ld_status link(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
   return LD_OK;
 }
 
+// Batched launches: `count` matrices, each found through recs[z] (F at f_off
+// bytes); their A / B operand rows a_zs / b_zs elements apart, their panel move
+// lists mv_zs bytes apart. The default is the single-matrix form.
+struct BatchSpec {
+  int64_t count = 1;
+  void* const* recs = nullptr;
+  int64_t f_off = 0, a_zs = 0, b_zs = 0, mv_zs = 0;
+};
+
 // Operand buffers of the trailing update: `cap` rows of bb elements in the
 // format of the mode (hi part, then the lo part for the split formats).
 struct OpBuf {
@@ -262,7 +369,7 @@ OpBuf op_buf(ld_mode mode, char* base, int64_t cap, int64_t bb) {
 template <typename T, int OUT>
 ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, int64_t row_begin,
                         int64_t row_end, void* ahi, void* alo, const int* moves, size_t smem,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, const BatchSpec& bs) {
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(trsm_kernel<T, kPanel / 32, OUT>,
@@ -272,8 +379,10 @@ ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, i
   }
   const int64_t rows = row_end - row_begin;
   ProfScope ps("trsm", stream, 3.0 * sizeof(T) * (double)rows * bb, (double)rows * bb * bb);
-  trsm_kernel<T, kPanel / 32, OUT><<<(unsigned)ceil_div(rows, kTrsmRowsPerCta), 256, smem, stream>>>(
-      F, ldf, (int)row_end, (int)s0, (int)bb, (int)m0, (int)row_begin, ahi, alo, moves);
+  dim3 grid((unsigned)ceil_div(rows, kTrsmRowsPerCta), 1, (unsigned)bs.count);
+  trsm_kernel<T, kPanel / 32, OUT><<<grid, 256, smem, stream>>>(
+      F, ldf, (int)row_end, (int)s0, (int)bb, (int)m0, (int)row_begin, ahi, alo, moves, bs.recs,
+      bs.f_off, bs.a_zs, bs.mv_zs);
   return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
 
@@ -281,23 +390,23 @@ ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, i
 template <typename T>
 ld_status launch_trsm(ld_mode mode, T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0,
                       int64_t row_begin, int64_t row_end, const OpBuf& a, const int* moves,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, const BatchSpec& bs = BatchSpec{}) {
   if (row_end <= row_begin) return LD_OK;
   const size_t smem = (size_t)bb * bb * sizeof(T);
   if constexpr (sizeof(T) == 8) {
     return launch_trsm_t<T, kOutT>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo, moves, smem,
-                                   stream);
+                                   stream, bs);
   } else {
     switch (mode) {
       case LD_F32_TF32:
         return launch_trsm_t<T, kOutTF32>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo, moves,
-                                          smem, stream);
+                                          smem, stream, bs);
       case LD_F32_3XTF32:
         return launch_trsm_t<T, kOutTF32x3>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo,
-                                            moves, smem, stream);
+                                            moves, smem, stream, bs);
       case LD_F32_BF16X3:
         return launch_trsm_t<T, kOutBF16x3>(F, ldf, s0, bb, m0, row_begin, row_end, a.hi, a.lo,
-                                            moves, smem, stream);
+                                            moves, smem, stream, bs);
       default:
         return LD_ERR_INVALID_ARG;
     }
@@ -307,23 +416,27 @@ ld_status launch_trsm(ld_mode mode, T* F, int64_t ldf, int64_t s0, int64_t bb, i
 // The panel rows transposed into the B operand (ncols rows of bb).
 template <typename T>
 ld_status launch_transpose(ld_mode mode, const T* F, int64_t ldf, int64_t s0, int64_t bb,
-                           int64_t ncols, const OpBuf& bo, cudaStream_t stream) {
-  dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(bb, 32));
+                           int64_t ncols, const OpBuf& bo, cudaStream_t stream,
+                           const BatchSpec& bs = BatchSpec{}) {
+  dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(bb, 32), (unsigned)bs.count);
   ProfScope ps("transpose", stream, (sizeof(T) + (op_split(mode) ? 2.0 : 1.0) * bo.es) * ncols * bb,
                0.0);
+  const int s = (int)s0, b = (int)bb, nc = (int)ncols;
   if constexpr (sizeof(T) == 8) {
-    transpose_rows_kernel<T, kOutT><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb, (int)ncols,
-                                                              bo.hi, bo.lo);
+    transpose_rows_kernel<T, kOutT><<<grid, 256, 0, stream>>>(F, ldf, s, b, nc, bo.hi, bo.lo,
+                                                              bs.recs, bs.f_off, bs.b_zs);
   } else {
     if (mode == LD_F32_TF32)
-      transpose_rows_kernel<T, kOutTF32><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
-                                                                   (int)ncols, bo.hi, bo.lo);
+      transpose_rows_kernel<T, kOutTF32><<<grid, 256, 0, stream>>>(F, ldf, s, b, nc, bo.hi, bo.lo,
+                                                                   bs.recs, bs.f_off, bs.b_zs);
     else if (mode == LD_F32_3XTF32)
-      transpose_rows_kernel<T, kOutTF32x3><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
-                                                                     (int)ncols, bo.hi, bo.lo);
+      transpose_rows_kernel<T, kOutTF32x3><<<grid, 256, 0, stream>>>(F, ldf, s, b, nc, bo.hi,
+                                                                     bo.lo, bs.recs, bs.f_off,
+                                                                     bs.b_zs);
     else
-      transpose_rows_kernel<T, kOutBF16x3><<<grid, 256, 0, stream>>>(F, ldf, (int)s0, (int)bb,
-                                                                     (int)ncols, bo.hi, bo.lo);
+      transpose_rows_kernel<T, kOutBF16x3><<<grid, 256, 0, stream>>>(F, ldf, s, b, nc, bo.hi,
+                                                                     bo.lo, bs.recs, bs.f_off,
+                                                                     bs.b_zs);
   }
   return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
@@ -479,6 +592,89 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
 }
 
 }  // namespace
+
+// Blocked sweep of `count` matrices of one size n (FP32 storage, tensor-core
+// trailing update), panel by panel across the whole batch: a single-CTA
+// cluster panel per matrix, then the batched multipliers, transposes and one
+// batched rank-b update. factors: the records (device array of pointers), or
+// nullptr for records in scratch.
+ld_status run_blocked_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n_arr,
+                              const int64_t* lda_arr, int64_t count, int64_t n, ld_mode mode,
+                              void* const* factors, double* signs, double* logabs,
+                              cudaStream_t stream) {
+  if (mode != LD_F32_TF32 && mode != LD_F32_3XTF32 && mode != LD_F32_BF16X3)
+    return LD_ERR_UNSUPPORTED;
+  if (count <= 0) return LD_OK;
+  if (n > 2048 || count > 65535) return LD_ERR_UNSUPPORTED;
+  const int b = kPanel;
+  const int64_t ldf = leading_dim(n);
+  const RecOffsets ro = record_offsets(n, mode);
+  const size_t rec_bytes = align_up(record_layout(n, mode, nullptr, nullptr), kAlign);
+  const size_t cl_stride = panel_cluster_scratch_bytes();
+  const size_t opb = align_up(op_bytes(mode, (int64_t)count * n, b), kAlign);
+  const size_t scratch_bytes = (factors ? 0 : (size_t)count * rec_bytes + align_up(count * 8, kAlign)) +
+                               (size_t)count * cl_stride + 2 * opb + 3 * kAlign;
+  void* scratch = nullptr;
+  ld_status st = scratch_alloc(&scratch, scratch_bytes, stream);
+  if (st != LD_OK) return st;
+  char* p = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
+  int* err = reinterpret_cast<int*>(p);  // the tensor-core kernel's timeout flag
+  p += kAlign;
+  if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) st = LD_ERR_CUDA;
+  void* const* recs = factors;
+  if (!factors) {
+    char* rec_base = p;
+    p += (size_t)count * rec_bytes;
+    void** ptrs = reinterpret_cast<void**>(p);
+    p += align_up(count * 8, kAlign);
+    fill_ptrs_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, stream>>>(rec_base, (int64_t)rec_bytes,
+                                                                        (int)count, ptrs);
+    recs = ptrs;
+  }
+  char* cl_scratch = p;
+  p += (size_t)count * cl_stride;
+  const OpBuf abuf = op_buf(mode, p, (int64_t)count * n, b);
+  p += opb;
+  const OpBuf bbuf = op_buf(mode, p, (int64_t)count * n, b);
+  {
+    dim3 grid((unsigned)ceil_div(n, 256), (unsigned)std::min<int64_t>(n, 64), (unsigned)count);
+    ProfScope ps("stage", stream, 8.0 * count * n * n, 0.0);
+    stage_batched_kernel<<<grid, 256, 0, stream>>>(A_ptrs, (int)a_dtype, n_arr, lda_arr, (int)n, ldf,
+                                                   (int)mode, recs, ro);
+    if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+  }
+  BatchSpec bs;
+  bs.count = count;
+  bs.recs = recs;
+  bs.f_off = ro.F;
+  bs.a_zs = n * b;
+  bs.b_zs = n * b;
+  bs.mv_zs = (int64_t)cl_stride;
+  for (int64_t s0 = 0; s0 < n && st == LD_OK; s0 += b) {
+    const int64_t bb = std::min<int64_t>(b, n - s0);
+    const int64_t m0 = n - s0;
+    st = launch_panel_cluster_batched(recs, ro, n, ldf, count, s0, bb, cl_scratch, stream);
+    const int64_t rows = n - s0 - bb;
+    if (st != LD_OK || rows <= 0) continue;
+    st = launch_trsm<float>(mode, nullptr, ldf, s0, bb, m0, s0 + bb, n, abuf,
+                            reinterpret_cast<const int*>(cl_scratch), stream, bs);
+    if (st == LD_OK)
+      st = launch_transpose<float>(mode, nullptr, ldf, s0, bb, rows, bbuf, stream, bs);
+    if (st != LD_OK) break;
+    const TcOperand oa{abuf.hi, abuf.lo, bb, n * bb};
+    const TcOperand ob{bbuf.hi, bbuf.lo, bb, n * bb};
+    st = rankb_tc(mode, oa, ob, (int)rows, (int)rows, (int)bb, nullptr, ldf, 0, (int)count, err,
+                  stream, recs, ro.F + (int64_t)(s0 + bb) * ldf * 4);
+  }
+  if (st == LD_OK) {
+    ProfScope ps("finalize", stream);
+    finalize_batched_kernel<<<(unsigned)ceil_div(count * 32, 256), 256, 0, stream>>>(
+        recs, ro, (int)n, (int)count, err, signs, logabs);
+    if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+  }
+  scratch_free(scratch, stream);
+  return st;
+}
 
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                       bool keep_factors, cudaStream_t stream) {

@@ -5,10 +5,12 @@
 //   TF32    one kind::tf32 MMA per K-step on the FP32 operands,
 //   3xTF32  A = Ah + Al, B = Bh + Bl split at TF32 precision; Al*Bh + Ah*Bl + Ah*Bh,
 //   BF16x3  the same split at BF16 precision with kind::f16 MMAs.
-// Per CTA: one 128 x BN output tile; warp 0 lane 0 issues TMA loads of 128-byte
-// K-chunks into a ring of shared-memory stages, warp 1 lane 0 issues tcgen05.mma
-// into a TMEM accumulator and frees stages with tcgen05.commit, then all four
-// warps read the accumulator (tcgen05.ld) and apply D -= acc.
+// Per CTA: up to TPC consecutive 128 x 128 output tiles. Warp 0 lane 0 issues TMA
+// loads of 128-byte K-chunks into a ring of shared-memory stages across the
+// CTA's tiles, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
+// accumulator buffers and frees stages with tcgen05.commit, and warps 2-5 drain
+// the other buffer (tcgen05.ld) and apply D -= acc, so one tile's epilogue
+// overlaps the next tile's loads and MMAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,18 +39,22 @@ struct TcCfg {
   static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
   static constexpr int NSUB = BK / KSTEP;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  // K-chunks rotate over NACC accumulators in TMEM (NACC x BN columns), summed in
-  // FP32 in the epilogue: each tensor-core accumulation chain is NACC times shorter.
-  static constexpr int NACC = 4;
-  static constexpr int TMEM_COLS = NACC * BN;  // 512: the whole TMEM of the SM
+  // K-chunks rotate over NACC accumulators (NACC x BN TMEM columns), summed in
+  // FP32 in the epilogue: each tensor-core accumulation chain is NACC times
+  // shorter. Two such buffers fill the SM's 512 TMEM columns.
+  static constexpr int NACC = 2;
+  static constexpr int ACC_COLS = NACC * BN;
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;
+  static constexpr int THREADS = 192;   // producer warp, MMA warp, 4 epilogue warps
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                    float* __restrict__ D, int64_t ldd, int64_t dstride, int M, int N, int K,
-                    int* __restrict__ err) {
+                    float* __restrict__ D, int64_t ldd, int64_t dstride,
+                    void* const* __restrict__ dptrs, int64_t doff, int M, int N, int K, int batch,
+                    int tpc, int* __restrict__ err) {
   using C = TcCfg<KIND>;
   constexpr uint32_t IDESC = tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, C::BM, C::BN);
   extern __shared__ uint8_t smem_raw[];
@@ -56,21 +62,29 @@ __global__ void __launch_bounds__(128, 1)
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* accf = empty + C::STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* accf = empty + C::STAGES;  // [2] accumulator buffer ready (MMA -> epilogue)
+  uint64_t* acce = accf + 2;           // [2] accumulator buffer drained (epilogue -> MMA)
+  uint64_t* done = acce + 2;           // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * C::BM, n0 = blockIdx.x * C::BN;
-  const int z = blockIdx.z;  // batch index (one matrix per z)
+  const int tn = (N + C::BN - 1) / C::BN, tm = (M + C::BM - 1) / C::BM;
+  const int per_z = tn * tm;
+  const int total = per_z * batch;
+  const int t_first = blockIdx.x * tpc;
+  const int ntile = min(tpc, total - t_first);
   const int nk = K / C::BK;
-  D += (int64_t)z * dstride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4);
+    }
+    tc::mbar_init(done, 1);
     tc::fence_mbar_init();
     tc::tma_prefetch_desc(&mAh);
     tc::tma_prefetch_desc(&mBh);
@@ -86,87 +100,128 @@ __global__ void __launch_bounds__(128, 1)
   int issued = 0;
 
   if (warp == 0 && lane == 0) {
-    // producer: one K-chunk of every operand tile per stage
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % C::STAGES, r = kc / C::STAGES;
-      if (!tc::mbar_wait(&empty[s], (r & 1) ^ 1, err)) break;
-      uint8_t* st = smem + s * C::STAGE_BYTES;
-      tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-      tc::tma_load_3d(st, &mAh, &full[s], kc * C::BK, m0, z);
-      tc::tma_load_3d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0, z);
-      if (C::NT == 2) {
-        tc::tma_load_3d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0, z);
-        tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0, z);
+    // producer: one K-chunk of every operand tile per stage, across the tiles
+    int g = 0;
+    bool ok = true;
+    for (int it = 0; it < ntile && ok; ++it) {
+      const int t = t_first + it, z = t / per_z, r = t % per_z;
+      const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = g % C::STAGES, rnd = g / C::STAGES;
+        if (!tc::mbar_wait(&empty[s], (rnd & 1) ^ 1, err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * C::STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+        tc::tma_load_3d(st, &mAh, &full[s], kc * C::BK, m0, z);
+        tc::tma_load_3d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0, z);
+        if (C::NT == 2) {
+          tc::tma_load_3d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0, z);
+          tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0, z);
+        }
+        issued = g + 1;
       }
-      ++issued;
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: K-chunk kc accumulates into accumulator kc % NACC
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % C::STAGES, r = kc / C::STAGES;
-      if (!tc::mbar_wait(&full[s], r & 1, err)) break;
+    // MMA issuer: tile it into buffer it & 1; K-chunk kc into accumulator kc % NACC
+    int g = 0;
+    bool ok = true;
+    for (int it = 0; it < ntile && ok; ++it) {
+      const int buf = it & 1, use = it >> 1;
+      if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, err)) break;
       tc::tc_fence_after();
-      const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
-      const uint32_t ah = st, al = st + C::A_BYTES;
-      const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
-      const uint32_t d = tmem + (uint32_t)((kc % C::NACC) * C::BN);
-      uint32_t acc = (kc >= C::NACC) ? 1u : 0u;  // first chunk of an accumulator overwrites
-#pragma unroll
-      for (int k = 0; k < C::NSUB; ++k) {
-        const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
-        if (KIND == kTF32) {
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-        } else if (KIND == kTF32x3) {
-          tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
-        } else {
-          tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = g % C::STAGES, rnd = g / C::STAGES;
+        if (!tc::mbar_wait(&full[s], rnd & 1, err)) {
+          ok = false;
+          break;
         }
-        acc = 1u;
+        tc::tc_fence_after();
+        const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t ah = st, al = st + C::A_BYTES;
+        const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
+        const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS + (kc % C::NACC) * C::BN);
+        uint32_t acc = (kc >= C::NACC) ? 1u : 0u;  // first chunk of an accumulator overwrites
+#pragma unroll
+        for (int k = 0; k < C::NSUB; ++k) {
+          const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
+          if (KIND == kTF32) {
+            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          } else if (KIND == kTF32x3) {
+            tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          } else {
+            tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+            tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+            tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          }
+          acc = 1u;
+        }
+        tc::mma_commit(&empty[s]);
       }
-      tc::mma_commit(&empty[s]);
+      if (ok) tc::mma_commit(&accf[buf]);
     }
-    tc::mma_commit(accf);
-  }
-  __syncwarp();
-
-  // epilogue: D -= acc, one TMEM lane (= one output row) per thread
-  const bool got = tc::mbar_wait(accf, 0, err);
-  __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
-  tc::tc_fence_after();
-  const bool clean = got && (*reinterpret_cast<volatile int*>(err) == 0);
-  const int row = m0 + warp * 32 + lane;
-  float* drow = D + (int64_t)row * ldd;
-  const int nacc = nk < C::NACC ? nk : C::NACC;
+    // every MMA issued has completed before TMEM is released
+    tc::mma_commit(done);
+    tc::mbar_wait(done, 0, err);
+  } else if (warp >= 2) {
+    // epilogue: D -= acc, one TMEM lane (= one output row) per thread; warp w
+    // may read TMEM lanes 32 * (w % 4) .. + 31
+    const int q = warp & 3;
+    for (int it = 0; it < ntile; ++it) {
+      const int buf = it & 1, use = it >> 1;
+      const bool got = tc::mbar_wait(&accf[buf], use & 1, err);
+      __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc::tc_fence_after();
+      const bool clean = *reinterpret_cast<volatile int*>(err) == 0;
+      const int t = t_first + it, z = t / per_z, r = t % per_z;
+      const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+      const int row = m0 + q * 32 + lane;
+      float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
+                        : D + (int64_t)z * dstride;
+      float* drow = dz + (int64_t)row * ldd;
+      const int nacc = nk < C::NACC ? nk : C::NACC;
 #pragma unroll 1
-  for (int c = 0; c < C::BN / 32; ++c) {
-    float a[32];
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
-    tc::tmem_ld32(lane_base, a);
-    for (int q = 1; q < nacc; ++q) {  // sum the accumulators in FP32 (round to nearest)
-      float b[32];
-      tc::tmem_ld32(lane_base + (uint32_t)(q * C::BN), b);
+      for (int c = 0; c < C::BN / 32; ++c) {
+        float a[32];
+        const uint32_t lane_base =
+            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::ACC_COLS + c * 32);
+        tc::tmem_ld32(lane_base, a);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) a[i] += b[i];
-    }
-    const int col0 = n0 + c * 32;
-    if (clean && row < M) {
-      if (col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0) {
+        for (int p = 1; p < C::NACC; ++p) {  // sum the accumulators in FP32 (round to nearest)
+          if (p < nacc) {
+            float b[32];
+            tc::tmem_ld32(lane_base + (uint32_t)(p * C::BN), b);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float4 v = *reinterpret_cast<float4*>(drow + col0 + 4 * q);
-          v.x -= a[4 * q + 0];
-          v.y -= a[4 * q + 1];
-          v.z -= a[4 * q + 2];
-          v.w -= a[4 * q + 3];
-          *reinterpret_cast<float4*>(drow + col0 + 4 * q) = v;
+            for (int i = 0; i < 32; ++i) a[i] += b[i];
+          }
         }
-      } else {
-        for (int q = 0; q < 32 && col0 + q < N; ++q) drow[col0 + q] -= a[q];
+        const int col0 = n0 + c * 32;
+        if (clean && row < M) {
+          if (col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0) {
+#pragma unroll
+            for (int v4 = 0; v4 < 8; ++v4) {
+              float4 v = *reinterpret_cast<float4*>(drow + col0 + 4 * v4);
+              v.x -= a[4 * v4 + 0];
+              v.y -= a[4 * v4 + 1];
+              v.z -= a[4 * v4 + 2];
+              v.w -= a[4 * v4 + 3];
+              *reinterpret_cast<float4*>(drow + col0 + 4 * v4) = v;
+            }
+          } else {
+#pragma unroll
+            for (int v1 = 0; v1 < 32; ++v1)
+              if (col0 + v1 < N) drow[col0 + v1] -= a[v1];
+          }
+        }
       }
+      // the buffer may be overwritten by the MMAs of tile it + 2
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[buf]);
     }
   }
 
@@ -304,7 +359,8 @@ namespace {
 
 template <int KIND>
 ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K, float* D,
-                    int64_t ldd, int64_t dstride, int batch, int* err, cudaStream_t stream) {
+                    int64_t ldd, int64_t dstride, void* const* dptrs, int64_t doff, int batch,
+                    int* err, cudaStream_t stream) {
   using C = TcCfg<KIND>;
   CUtensorMap mAh, mAl, mBh, mBl;
   if (!make_map(&mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
@@ -325,12 +381,17 @@ ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K,
       return LD_ERR_CUDA;
     attr_set = true;
   }
-  dim3 grid((unsigned)ceil_div(N, C::BN), (unsigned)ceil_div(M, C::BM), (unsigned)batch);
+  const int64_t tiles = ceil_div(N, C::BN) * ceil_div(M, C::BM) * (int64_t)batch;
+  // tiles per CTA: one while the grid is within two waves, else up to four
+  // (their epilogues overlap the next tile's loads and MMAs; CTAs stay short so
+  // concurrent critical-path kernels still find SMs)
+  const int64_t sm = device_sm_count();
+  const int tpc = tiles >= 8 * sm ? 4 : tiles >= 4 * sm ? 2 : 1;
   ProfScope ps("rankb_tc", stream,
                (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),
                (double)batch * 2.0 * M * N * K);
-  rankb_tc_kernel<KIND><<<grid, 128, C::SMEM, stream>>>(mAh, mAl, mBh, mBl, D, ldd, dstride, M, N,
-                                                        K, err);
+  rankb_tc_kernel<KIND><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM, stream>>>(
+      mAh, mAl, mBh, mBl, D, ldd, dstride, dptrs, doff, M, N, K, batch, tpc, err);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }
@@ -414,16 +475,17 @@ ld_status rankb_prepare(ld_mode mode, int64_t rows, int64_t K, const float* src,
 // batched over `batch` matrices (operand and D strides in elements).
 ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, int N, int K,
                    float* D, int64_t ldd, int64_t dstride, int batch, int* err,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, void* const* dptrs, int64_t doff) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return LD_OK;
-  if (K % 64 != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0) return LD_ERR_UNSUPPORTED;
+  if (K % 64 != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0 || (doff & 3) != 0)
+    return LD_ERR_UNSUPPORTED;
   switch (mode) {
     case LD_F32_TF32:
-      return launch_tc<kTF32>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
+      return launch_tc<kTF32>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream);
     case LD_F32_3XTF32:
-      return launch_tc<kTF32x3>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
+      return launch_tc<kTF32x3>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream);
     case LD_F32_BF16X3:
-      return launch_tc<kBF16x3>(a, b, M, N, K, D, ldd, dstride, batch, err, stream);
+      return launch_tc<kBF16x3>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream);
     default:
       return LD_ERR_INVALID_ARG;
   }

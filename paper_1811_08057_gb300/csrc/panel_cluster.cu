@@ -62,6 +62,12 @@ struct ClusterArgs {
   int* moves;       // [1 + 2 * 2 * kBMax]: count, then (dst, src) position pairs
   int* dlist;       // [1 + 3 * 2 * kBMax]: count, then (position, new label, old label)
   int logsum;       // 1: accumulate the panel's sign and log-sum here; 0: the caller does
+  // batched form (recs != nullptr): cluster z works on the matrix whose record
+  // starts at recs[z] (parts at the offsets ro); its moves and dlist sit
+  // scr_stride bytes further per matrix
+  void* const* recs;
+  RecOffsets ro;
+  int64_t scr_stride;
 };
 
 // K: positions per thread (W <= K * kCT). The thread's values of the inner
@@ -71,6 +77,17 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
+  if (a.recs) {
+    const int z = blockIdx.x / CL;
+    char* b = static_cast<char*>(a.recs[z]);
+    a.F = reinterpret_cast<float*>(b + a.ro.F);
+    a.colperm = reinterpret_cast<int*>(b + a.ro.colperm);
+    a.pivpos = reinterpret_cast<int*>(b + a.ro.pivpos);
+    a.pivval = reinterpret_cast<double*>(b + a.ro.pivval);
+    a.st = reinterpret_cast<SweepState*>(b + a.ro.state);
+    a.moves = reinterpret_cast<int*>(reinterpret_cast<char*>(a.moves) + z * a.scr_stride);
+    a.dlist = reinterpret_cast<int*>(reinterpret_cast<char*>(a.dlist) + z * a.scr_stride);
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int W = a.W, bb = a.bb, m0 = a.m0;
   const int j_lo = c * W, j_hi = min(m0, j_lo + W);
@@ -479,6 +496,35 @@ __global__ void apply_moves_kernel(float* __restrict__ F, int64_t ldf, int r0, i
   }
 }
 
+// Batched form: matrix blockIdx.y (record recs[y], F at f_off bytes), rows
+// [0, r1), the matrix's move list at moves + y * stride bytes.
+__global__ void apply_moves_batched_kernel(void* const* __restrict__ recs, int64_t f_off,
+                                           int64_t ldf, int r1, const int* __restrict__ moves,
+                                           int64_t stride) {
+  const int z = blockIdx.y;
+  float* F = reinterpret_cast<float*>(static_cast<char*>(recs[z]) + f_off);
+  const int* mv = reinterpret_cast<const int*>(reinterpret_cast<const char*>(moves) + z * stride);
+  const int nm = mv[0];
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = wid; r < r1; r += nw) {
+    float* row = F + (int64_t)r * ldf;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = lane + 32 * q;
+      v[q] = (k < nm) ? row[mv[2 + 2 * k]] : 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = lane + 32 * q;
+      if (k < nm) row[mv[1 + 2 * k]] = v[q];
+    }
+  }
+}
+
 }  // namespace
 
 size_t panel_cluster_scratch_bytes() {
@@ -536,7 +582,8 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     int* dlist = reinterpret_cast<int*>(static_cast<char*>(scratch) +
                                         align_up((1 + 4 * kBMax) * 4, kAlign));
     ClusterArgs a{static_cast<float*>(r.F), r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
-                  r.colperm, r.pivpos, r.pivval, r.state, moves, dlist, defer_logsum ? 0 : 1};
+                  r.colperm, r.pivpos, r.pivval, r.state, moves, dlist, defer_logsum ? 0 : 1,
+                  nullptr, RecOffsets{}, 0};
     cudaError_t e;
     {
       ProfScope ps("panel", stream, 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
@@ -562,6 +609,56 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
   }
   if (tried && cl_ok < 0) cl_ok = 0;  // no cluster of 16 or 8 forms on this device
   return LD_ERR_UNSUPPORTED;
+}
+
+// Batched form: one single-CTA cluster per matrix, `count` matrices of size n
+// (records at recs[z]); scratch holds count x panel_cluster_scratch_bytes().
+// The panels' sign and log-sum are left to the caller. Rows before the panel
+// (the factor record) receive the composed moves.
+ld_status launch_panel_cluster_batched(void* const* recs, const RecOffsets& ro, int64_t n,
+                                       int64_t ldf, int64_t count, int64_t s0, int64_t bb,
+                                       void* scratch, cudaStream_t stream) {
+  if (bb > kBMax || count <= 0) return LD_ERR_UNSUPPORTED;
+  const int64_t m0 = n - s0;
+  const int64_t W = m0;
+  if (W > 8 * kCT) return LD_ERR_UNSUPPORTED;
+  const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
+  void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<1>
+                              : K == 2 ? panel_cluster_kernel<2>
+                              : K == 4 ? panel_cluster_kernel<4>
+                                       : panel_cluster_kernel<8>;
+  const size_t smem = kKI * kKI * 4 + (size_t)kBMax * kKI * 4 + (size_t)W * 4;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)count);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int64_t stride = (int64_t)panel_cluster_scratch_bytes();
+  int* moves = static_cast<int*>(scratch);
+  int* dlist = reinterpret_cast<int*>(static_cast<char*>(scratch) +
+                                      align_up((1 + 4 * kBMax) * 4, kAlign));
+  ClusterArgs a{nullptr, ldf, (int)n, (int)s0, (int)bb, (int)m0, (int)W, nullptr, nullptr,
+                nullptr, nullptr, moves, dlist, 0, recs, ro, stride};
+  {
+    ProfScope ps("panel", stream, (double)count * 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
+                 (double)count * bb * bb * m0);
+    if (cudaLaunchKernelEx(&cfg, kern, a) != cudaSuccess) return LD_ERR_CUDA;
+  }
+  if (s0 > 0) {
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(s0, 8), 64), (unsigned)count);
+    ProfScope ps("apply_moves", stream, 8.0 * count * s0 * 2 * bb, 0.0);
+    apply_moves_batched_kernel<<<grid, 256, 0, stream>>>(recs, ro.F, ldf, (int)s0, moves, stride);
+    if (cudaGetLastError() != cudaSuccess) return LD_ERR_CUDA;
+  }
+  return LD_OK;
 }
 
 // Sign and compensated log-sum of the panel's pivots (Sec. 2.4, Eq. (2)): one

@@ -83,6 +83,22 @@ inline size_t record_layout(int64_t n, ld_mode mode, void* base, Record* r) {
   return off;
 }
 
+// Byte offsets of a record's parts (the layout of record_layout), for kernels
+// that find each matrix's record through a device array of base pointers.
+struct RecOffsets {
+  int64_t header, F, colperm, pivpos, pivval, state;
+};
+inline RecOffsets record_offsets(int64_t n, ld_mode mode) {
+  Record r;
+  char* const base = reinterpret_cast<char*>(kAlign);  // any aligned address: only differences used
+  record_layout(n, mode, base, &r);
+  return RecOffsets{reinterpret_cast<char*>(r.header) - base, static_cast<char*>(r.F) - base,
+                    reinterpret_cast<char*>(r.colperm) - base,
+                    reinterpret_cast<char*>(r.pivpos) - base,
+                    reinterpret_cast<char*>(r.pivval) - base,
+                    reinterpret_cast<char*>(r.state) - base};
+}
+
 int device_sm_count();
 
 // Tuning table (ld_set_tuning): blocked panel width, batched panel depth per
@@ -131,9 +147,10 @@ struct TcOperand {
   int64_t ld;
   int64_t bstride;
 };
+// D of matrix z: D + z * dstride, or, with dptrs, (char*)dptrs[z] + doff bytes.
 ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, int N, int K,
                    float* D, int64_t ldd, int64_t dstride, int batch, int* err,
-                   cudaStream_t stream);
+                   cudaStream_t stream, void* const* dptrs = nullptr, int64_t doff = 0);
 size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K);
 // Bytes of one rows x K operand in the mode's tensor-core format (hi, then lo).
 size_t rankb_operand_bytes(ld_mode mode, int64_t rows, int64_t K);
@@ -161,8 +178,17 @@ size_t panel_cluster_scratch_bytes();
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
                                void* scratch, bool defer_logsum, cudaStream_t stream);
 ld_status launch_panel_logsum(const Record& r, int64_t s0, int64_t bb, cudaStream_t stream);
+ld_status launch_panel_cluster_batched(void* const* recs, const RecOffsets& ro, int64_t n,
+                                       int64_t ldf, int64_t count, int64_t s0, int64_t bb,
+                                       void* scratch, cudaStream_t stream);
 
 // ---- blocked path (blocked.cu) ----
+// count matrices of one size n in an FP32 tensor-core mode, panel by panel
+// across the batch; factors = the records (device pointer array) or nullptr.
+ld_status run_blocked_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n_arr,
+                              const int64_t* lda_arr, int64_t count, int64_t n, ld_mode mode,
+                              void* const* factors, double* signs, double* logabs,
+                              cudaStream_t stream);
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                       bool keep_factors, cudaStream_t stream);
 
