@@ -250,17 +250,18 @@ def other_paths(pk, _lib, A, main_mode, dev, err_gold=None):
         X = ((Q * lam[:, None, :]) @ Q.transpose(1, 2)).float()
         del Q, R
 
-        def fb():
-            Xg = X.detach().requires_grad_(True)
-            out = pk.logabsdet(Xg, "f32_plain")
-            out.sum().backward()
-            return Xg.grad
-        ms, _ = time_call(fb, 1, 2, dev)
-        res["grad_256x1024_f32"] = {"ms_forward_backward": ms,
-                                    "fwd_bwd_tflops": (B * (2 * n ** 3 / 3 + 2 * n ** 3)) /
-                                    (ms * 1e-3) / 1e12}
+        for gm in ("f32_3xtf32", "f32_plain"):
+            def fb():
+                Xg = X.detach().requires_grad_(True)
+                out = pk.logabsdet(Xg, gm)
+                out.sum().backward()
+                return Xg.grad
+            ms, _ = time_call(fb, 1, 2, dev)
+            res[f"grad_256x1024_{gm}"] = {"ms_forward_backward": ms,
+                                          "fwd_bwd_tflops": (B * (2 * n ** 3 / 3 + 2 * n ** 3)) /
+                                          (ms * 1e-3) / 1e12}
     except Exception as ex:
-        res["grad_256x1024_f32"] = {"error": str(ex)[:200]}
+        res["grad_256x1024"] = {"error": str(ex)[:200]}
     return res
 
 
@@ -427,11 +428,12 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
 
         def step():
             Xg = X.detach().requires_grad_(True)
-            y = pk.logabsdet(Xg, "f32_plain")
+            y = pk.logabsdet(Xg, "f32_3xtf32")
             y.sum().backward()
             return Xg.grad
-        units, unit, kernel = float(B), "matrices/s", "batched"
-        wl = "256 SPD 1024x1024 FP32, eigenvalues log-uniform in [1e-2,1], seed 4: log|det| + gradient"
+        units, unit, kernel = float(B), "matrices/s", "rankb_tc"
+        wl = ("256 SPD 1024x1024 FP32, eigenvalues log-uniform in [1e-2,1], seed 4: log|det| "
+              "(batched blocked sweep, 3xTF32) + gradient")
         flop = B * (2.0 * n ** 3 / 3.0 + 2.0 * n ** 3)
     for _ in range(args.warmup):
         step()
@@ -466,6 +468,10 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
     alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     k_flop = flop * args.steps if args.workload == "batched4096" else None
     roof = None
+    if args.workload != "batched4096" and k_ms > 0:
+        kb, kf = _lib.ld_profile_work(kernel)
+        roof = make_roofline(kernel, "f32_3xtf32", kb, kf, k_ms, k_launches, args.steps)
+        roof["kernel_shares"] = shares
     if k_flop and k_ms > 0:
         ach = k_flop / (k_ms * 1e-3) / 1e12
         roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": alu_peak,

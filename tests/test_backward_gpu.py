@@ -99,9 +99,11 @@ def test_batched_factor_records_reconstruct():
         assert np.abs(L @ U - AQJ).max() <= 1e-12 * n
 
 
-def test_backward_config_256x1024_sampled():
+@pytest.mark.parametrize("mode", ["f32_plain", "f32_3xtf32"])
+def test_backward_config_256x1024_sampled(mode):
     """256 SPD 1024^2 (eigenvalues log-uniform in [1e-2, 1]), FP32: batched forward
-    and backward; 4 sampled gradients against the FP64 inverse."""
+    (persistent plain sweep, or the batched blocked 3xTF32 sweep) and backward; 4
+    sampled gradients against the FP64 inverse."""
     B, n = 256, 1024
     g = torch.Generator(device="cuda").manual_seed(4)
     lam = 10.0 ** (-2.0 * torch.rand(B, n, generator=g, device="cuda", dtype=torch.float64))
@@ -111,7 +113,7 @@ def test_backward_config_256x1024_sampled():
     A = (0.5 * (A + A.transpose(1, 2))).float()
     del Q, R
     X = A.clone().requires_grad_(True)
-    out = api.logabsdet(X, "f32_plain")
+    out = api.logabsdet(X, mode)
     out.sum().backward()
     torch.cuda.synchronize()
     exact = torch.log(lam).sum(dim=1)
