@@ -69,14 +69,16 @@ __global__ void unpack_kernel(const void* const* __restrict__ recs, int n, int n
 }
 
 // Per-row substitution on column block I of rows [0, M) of every matrix:
-// lower: x L_II^T = b (forward, divides by the pivots); upper: x U_II^T = b
-// (backward, unit diagonal). One warp per row; lane k holds entries k, k+32, ...
+// lower: x L_II^T = b (forward; the pivots' reciprocals are formed once per
+// block); upper: x U_II^T = b (backward, unit diagonal). Each warp solves two rows
+// interleaved; lane k holds entries k, k+32, ... of both.
 template <typename T, bool LOWER, bool SPLIT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     rowsolve_kernel(const void* const* __restrict__ recs, int n, int np, int64_t ldf, int I,
                     int M, T* __restrict__ Yv, T* __restrict__ Yh, T* __restrict__ Yl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*S)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // kNB x (kNB + 1)
+  T* rdiag = reinterpret_cast<T*>(smem_raw) + kNB * (kNB + 1);  // kNB reciprocals of the pivots
   const int z = blockIdx.y;
   const T* F = reinterpret_cast<const T*>(static_cast<const char*>(recs[z]) + kAlign);
   const int c0 = I * kNB;
@@ -85,25 +87,40 @@ __global__ void __launch_bounds__(256)
     S[k][j] = lu_entry(F, ldf, n, c0 + k, c0 + j, LOWER);
   }
   __syncthreads();
+  if (LOWER && threadIdx.x < kNB) rdiag[threadIdx.x] = T(1) / S[threadIdx.x][threadIdx.x];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)z * np * np;
   constexpr int KQ = kNB / 32;
-  for (int r = blockIdx.x * 8 + (threadIdx.x >> 5); r < M; r += gridDim.x * 8) {
-    T* row = Yv + base + (int64_t)r * np + c0;
-    T x[KQ];
+  for (int r = 2 * (blockIdx.x * 8 + (threadIdx.x >> 5)); r < M; r += gridDim.x * 16) {
+    const bool two = r + 1 < M;
+    T* row0 = Yv + base + (int64_t)r * np + c0;
+    T* row1 = two ? row0 + np : row0;
+    T x[KQ], y[KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) x[q] = row[lane + 32 * q];
+    for (int q = 0; q < KQ; ++q) {
+      x[q] = row0[lane + 32 * q];
+      y[q] = row1[lane + 32 * q];
+    }
     if (LOWER) {
 #pragma unroll
       for (int qq = 0; qq < KQ; ++qq) {
         for (int tt = 0; tt < 32; ++tt) {
           const int k = qq * 32 + tt;
-          if (lane == tt) x[qq] = x[qq] / S[k][k];
+          if (lane == tt) {
+            x[qq] = x[qq] * rdiag[k];
+            y[qq] = y[qq] * rdiag[k];
+          }
           const T xk = __shfl_sync(0xffffffffu, x[qq], tt);
+          const T yk = __shfl_sync(0xffffffffu, y[qq], tt);
 #pragma unroll
           for (int q = qq; q < KQ; ++q) {
             const int m = lane + 32 * q;
-            if (m > k) x[q] = fma_t(-S[m][k], xk, x[q]);
+            if (m > k) {
+              const T smk = S[m][k];
+              x[q] = fma_t(-smk, xk, x[q]);
+              y[q] = fma_t(-smk, yk, y[q]);
+            }
           }
         }
       }
@@ -113,10 +130,15 @@ __global__ void __launch_bounds__(256)
         for (int tt = 31; tt >= 0; --tt) {
           const int k = qq * 32 + tt;
           const T xk = __shfl_sync(0xffffffffu, x[qq], tt);
+          const T yk = __shfl_sync(0xffffffffu, y[qq], tt);
 #pragma unroll
           for (int q = 0; q <= qq; ++q) {
             const int m = lane + 32 * q;
-            if (m < k) x[q] = fma_t(-S[m][k], xk, x[q]);
+            if (m < k) {
+              const T smk = S[m][k];
+              x[q] = fma_t(-smk, xk, x[q]);
+              y[q] = fma_t(-smk, yk, y[q]);
+            }
           }
         }
       }
@@ -124,12 +146,18 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
       const int idx = lane + 32 * q;
-      row[idx] = x[q];
+      row0[idx] = x[q];
+      if (two) row1[idx] = y[q];
       if constexpr (SPLIT) {
         float h, lo;
         tf32_split((float)x[q], h, lo);
         Yh[base + (int64_t)r * np + c0 + idx] = h;
         Yl[base + (int64_t)r * np + c0 + idx] = lo;
+        if (two) {
+          tf32_split((float)y[q], h, lo);
+          Yh[base + (int64_t)(r + 1) * np + c0 + idx] = h;
+          Yl[base + (int64_t)(r + 1) * np + c0 + idx] = lo;
+        }
       }
     }
   }
@@ -251,7 +279,7 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
         np, reinterpret_cast<double*>(Yv + d_off), np, bstride, (int)M, (int)N, (int)K);
     return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
   };
-  const size_t solve_smem = (size_t)kNB * (kNB + 1) * sizeof(T);
+  const size_t solve_smem = (size_t)kNB * (kNB + 2) * sizeof(T);
   if (cudaFuncSetAttribute(rowsolve_kernel<T, true, SPLIT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem) != cudaSuccess ||
       cudaFuncSetAttribute(rowsolve_kernel<T, false, SPLIT>,
