@@ -48,7 +48,6 @@ constexpr int kCT = 256;    // threads per CTA
 constexpr int kKI = 16;     // pivots per inner block
 constexpr int kBMax = 128;  // largest panel
 constexpr int kCLMax = 16;  // largest cluster
-constexpr int kRU = 8;      // rows per register tile of the rows-below update
 
 struct ClusterArgs {
   float* F;
@@ -74,6 +73,8 @@ struct ClusterArgs {
 // block live in registers: x[i][k] = row i at position c*W + tid + k*kCT.
 template <int K>
 __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
+  // rows per register tile of the rows-below update (deeper while registers allow)
+  constexpr int kRU = K <= 2 ? 16 : 8;
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
