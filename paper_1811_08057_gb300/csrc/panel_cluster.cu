@@ -69,6 +69,25 @@ struct ClusterArgs {
   int64_t scr_stride;
 };
 
+// Row t of the block factored (x[t] = r) and the rank-1 update of its later
+// rows with multipliers pcv, for pivot row T of the block: static register
+// indices (one instance per T, picked by a switch on the uniform pivot index).
+template <int T, int K>
+__device__ __forceinline__ void block_update(float (&x)[kKI][K], float (&cur)[K],
+                                             const float (&r)[K], const float (&pcv)[kKI], int kb,
+                                             const bool (&act)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (act[k]) {
+      x[T][k] = r[k];
+#pragma unroll
+      for (int i = T + 1; i < kKI; ++i)
+        if (i < kb) x[i][k] = fmaf(-pcv[i], r[k], x[i][k]);
+      if (T + 1 < kKI) cur[k] = x[T + 1 < kKI ? T + 1 : T][k];
+    }
+  }
+}
+
 // K: positions per thread (W <= K * kCT). The thread's values of the inner
 // block live in registers: x[i][k] = row i at position c*W + tid + k*kCT.
 template <int K>
@@ -263,18 +282,28 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
       // then the rank-1 update of the block's later rows, position by position
       const int jend = min(w_own, m - 1 - j_lo);
+      float rk[K];
+      bool act[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
-        if (j < jend) {
-          const float r = __fdiv_rn((j == jl) ? lc[t] : cur[k], pf);
-#pragma unroll
-          for (int i = 0; i < kKI; ++i) {
-            if (i == t) x[i][k] = r;
-            if (i > t && i < kb) x[i][k] = fmaf(-pcv[i], r, x[i][k]);
-            if (i == t + 1) cur[k] = x[i][k];
-          }
-        }
+        act[k] = j < jend;
+        rk[k] = act[k] ? __fdiv_rn((j == jl) ? lc[t] : cur[k], pf) : 0.f;
+      }
+      switch (t) {
+#define LD_BLOCK_UPDATE_CASE(T) \
+  case T:                       \
+    block_update<T, K>(x, cur, rk, pcv, kb, act); \
+    break;
+        LD_BLOCK_UPDATE_CASE(0) LD_BLOCK_UPDATE_CASE(1) LD_BLOCK_UPDATE_CASE(2)
+        LD_BLOCK_UPDATE_CASE(3) LD_BLOCK_UPDATE_CASE(4) LD_BLOCK_UPDATE_CASE(5)
+        LD_BLOCK_UPDATE_CASE(6) LD_BLOCK_UPDATE_CASE(7) LD_BLOCK_UPDATE_CASE(8)
+        LD_BLOCK_UPDATE_CASE(9) LD_BLOCK_UPDATE_CASE(10) LD_BLOCK_UPDATE_CASE(11)
+        LD_BLOCK_UPDATE_CASE(12) LD_BLOCK_UPDATE_CASE(13) LD_BLOCK_UPDATE_CASE(14)
+        LD_BLOCK_UPDATE_CASE(15)
+#undef LD_BLOCK_UPDATE_CASE
+        default:
+          break;
       }
     }
     // after a failed pivot or a timeout the CTAs only keep the barrier sequence
