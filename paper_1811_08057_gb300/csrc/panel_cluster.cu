@@ -261,8 +261,11 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       float pcv[kKI];
 #pragma unroll
       for (int i = 0; i < kKI; ++i) pcv[i] = pc[i];
-      if (l != m - 1) {
-        // exchange of columns l and m-1 (Sec. 2.4), by their owners
+      const bool own_l = jl >= 0 && jl < w_own && jl % kCT == tid;
+      const bool own_m = jm >= 0 && jm < w_own && jm % kCT == tid;
+      if (l != m - 1 && (own_l || own_m)) {
+        // exchange of columns l and m-1 (Sec. 2.4), by their owners (one or two
+        // threads of the CTA)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int j = tid + k * kCT;
@@ -335,13 +338,19 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         p = mq - 1 - (lane - kb);
       bool rep = lane < 2 * kb;
       int src = p;
-      for (int t = kb - 1; t >= 0; --t) {
-        const int x = __shfl_sync(0xffffffffu, sw, t), y = mq - 1 - t;
-        if ((t < lane && x == p) || (kb + t < lane && y == p)) rep = false;
-        if (src == x)
-          src = y;
-        else if (src == y)
-          src = x;
+      int xs[kKI];
+#pragma unroll
+      for (int t = 0; t < kKI; ++t) xs[t] = __shfl_sync(0xffffffffu, sw, t);
+#pragma unroll
+      for (int t = kKI - 1; t >= 0; --t) {
+        if (t < kb) {
+          const int x = xs[t], y = mq - 1 - t;
+          if ((t < lane && x == p) || (kb + t < lane && y == p)) rep = false;
+          if (src == x)
+            src = y;
+          else if (src == y)
+            src = x;
+        }
       }
       const bool moved = rep && src != p;
       const unsigned bm = __ballot_sync(0xffffffffu, moved);
