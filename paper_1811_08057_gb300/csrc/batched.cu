@@ -40,6 +40,11 @@ struct BatchedArgs {
   double* logabs;
   void* const* factors;  // optional: one factor record per matrix (else nullptr)
   int mode;
+  // FP32: pivots (value, position) and flags per matrix, for the finalize kernel
+  // (the pivots go to the record when there is one)
+  double* pv;            // count x n_max
+  int* pp;               // count x n_max
+  int* mflags;           // count
   int kb_table[kTuneBuckets];  // panel depth per size class (<= kKB)
 };
 
@@ -93,6 +98,12 @@ __global__ void __launch_bounds__(kBT)
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
   __shared__ int s_swap[kKB];
+  // FP32 pivot search: warp candidates, their columns and the boundary column
+  // (by pivot parity)
+  __shared__ KCand wredk[2][kBT / 32];
+  __shared__ float wcolb[2][kBT / 32][kKB];
+  __shared__ float lcolb[2][kKB];
+  __shared__ int lastlab[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* const ws_W = ws ? ws + (int64_t)blockIdx.x * n_max * args.ldw : nullptr;
@@ -134,6 +145,8 @@ __global__ void __launch_bounds__(kBT)
       q += align_up((size_t)n * 4, kAlign);
       rec_pivval = reinterpret_cast<double*>(q);
     }
+    double* piv_v = rec ? rec_pivval : (args.pv ? args.pv + (int64_t)mat * n_max : nullptr);
+    int* piv_p = rec ? rec_pivpos : (args.pp ? args.pp + (int64_t)mat * n_max : nullptr);
     // stage the matrix into the CTA's workspace (a0)
     for (int i = warp; i < n; i += kBT / 32)
       for (int j = lane; j < n; j += 32)
@@ -154,84 +167,153 @@ __global__ void __launch_bounds__(kBT)
         P[t * pw + j] = W[(int64_t)(s0 + t) * ldw + j];
       }
       __syncthreads();
-      for (int t = 0; t < bb; ++t) {
-        const int m = m0 - t;
-        // pivot column of panel row t (Sec. 2.2), ties to the smallest label: warp 0
-        // (FP32 storage compares in FP32: exact, and off the FP64 pipe)
-        if (warp == 0) {
-          Cand c;
-          if constexpr (sizeof(T) == 4) {
-            CandF cf;
-            candf_init(cf);
-            for (int j = lane; j < m; j += 32) candf_offer(cf, (float)P[t * pw + j], label[j], j);
-            candf_warp_reduce(cf);
-            c.absv = cf.absv;
-            c.v = cf.v;
-            c.label = cf.label;
-            c.pos = cf.pos;
-            c.nan = cf.nan;
-          } else {
-            cand_init(c);
-            for (int j = lane; j < m; j += 32) cand_offer(c, (double)P[t * pw + j], label[j], j);
-            cand_warp_reduce(c);
+      if constexpr (sizeof(T) == 4) {
+        // FP32: column ownership (thread x owns columns x, x + kBT, ...), one CTA
+        // barrier per pivot; the pivots' sign and log-sum are left to the
+        // finalize kernel (the same steps in pivot order)
+        int bad = 0;
+        for (int t = 0; t < bb; ++t) {
+          const int m = m0 - t;
+          const int par = t & 1;
+          KCand cd;
+          kc_init(cd);
+          for (int j = tid; j < m; j += kBT) kc_offer(cd, (float)P[t * pw + j], label[j], j);
+          const int src = kc_warp_best(cd);
+          if (lane == src && cd.key != 0u) {
+            const int jc = kc_pos(cd);
+            for (int i = 0; i < bb; ++i) wcolb[par][warp][i] = (float)P[i * pw + jc];
           }
-          if (lane == 0) {
-            if (c.nan || c.pos < 0 || c.absv == 0.0) {
-              s_bad = c.nan ? kFlagNaN : kFlagSingular;
+          if ((m - 1) % kBT == tid) {
+            for (int i = 0; i < bb; ++i) lcolb[par][i] = (float)P[i * pw + m - 1];
+            lastlab[par] = label[m - 1];
+          }
+          if (lane == 0) wredk[par][warp] = cd;
+          __syncthreads();
+          KCand cb;
+          if (lane < kBT / 32)
+            cb = wredk[par][lane];
+          else
+            kc_init(cb);
+          const int wb = kc_warp_best(cb);
+          if (cb.key == kKeyNaN || cb.key <= 1u) {
+            bad = (cb.key == kKeyNaN) ? kFlagNaN : kFlagSingular;
+            break;
+          }
+          const int l = kc_pos(cb);
+          const float pf = kc_value(cb);
+          if (tid == 0) {
+            s_swap[t] = l;
+            if (piv_v) {
+              piv_v[s0 + t] = (double)pf;
+              piv_p[s0 + t] = l;
+            }
+          }
+          const float* pc = wcolb[par][wb];  // multipliers of the panel rows
+          const float* lc = lcolb[par];      // boundary column
+          if (l != m - 1) {
+            // exchange of columns l and m-1 (Sec. 2.4), each by its owner
+            if (l % kBT == tid) {
+              for (int i = 0; i < bb; ++i)
+                if (i != t) P[i * pw + l] = (T)lc[i];
+              label[l] = lastlab[par];
+            }
+            if ((m - 1) % kBT == tid) {
+              for (int i = 0; i < bb; ++i) P[i * pw + m - 1] = (T)pc[i];
+              label[m - 1] = cb.label;
+            }
+          }
+          // row t factored (IEEE FP32 divide), rank-1 update of the later panel
+          // rows (Eq. (2)), own columns
+          for (int j = tid; j < m - 1; j += kBT) {
+            const float v = (j == l) ? lc[t] : (float)P[t * pw + j];
+            const float r = __fdiv_rn(v, pf);
+            P[t * pw + j] = (T)r;
+            for (int i = t + 1; i < bb; ++i)
+              P[i * pw + j] = (T)fmaf(-pc[i], r, (float)P[i * pw + j]);
+          }
+        }
+        if (tid == 0) s_bad = bad;
+        __syncthreads();
+      } else {
+        for (int t = 0; t < bb; ++t) {
+          const int m = m0 - t;
+          // pivot column of panel row t (Sec. 2.2), ties to the smallest label: warp 0
+          // (FP32 storage compares in FP32: exact, and off the FP64 pipe)
+          if (warp == 0) {
+            Cand c;
+            if constexpr (sizeof(T) == 4) {
+              CandF cf;
+              candf_init(cf);
+              for (int j = lane; j < m; j += 32) candf_offer(cf, (float)P[t * pw + j], label[j], j);
+              candf_warp_reduce(cf);
+              c.absv = cf.absv;
+              c.v = cf.v;
+              c.label = cf.label;
+              c.pos = cf.pos;
+              c.nan = cf.nan;
             } else {
-              const int l = c.pos;
-              double sg = sign;
-              if (c.v < 0.0) sg = -sg;
-              if (((m + 1) & 1) != 0) sg = -sg;
-              if (l != m - 1) sg = -sg;
-              sign = sg;
-              const double x = log(fabs(c.v));
-              const double tt = sum + x;
-              if (fabs(sum) >= fabs(x))
-                comp += (sum - tt) + x;
-              else
-                comp += (x - tt) + sum;
-              sum = tt;
-              const int lab = label[l];
-              label[l] = label[m - 1];
-              label[m - 1] = lab;
-              s_swap[t] = l;
-              s_l = l;
-              s_p = c.v;
-              if (rec) {
-                rec_pivpos[s0 + t] = l;
-                rec_pivval[s0 + t] = c.v;
+              cand_init(c);
+              for (int j = lane; j < m; j += 32) cand_offer(c, (double)P[t * pw + j], label[j], j);
+              cand_warp_reduce(c);
+            }
+            if (lane == 0) {
+              if (c.nan || c.pos < 0 || c.absv == 0.0) {
+                s_bad = c.nan ? kFlagNaN : kFlagSingular;
+              } else {
+                const int l = c.pos;
+                double sg = sign;
+                if (c.v < 0.0) sg = -sg;
+                if (((m + 1) & 1) != 0) sg = -sg;
+                if (l != m - 1) sg = -sg;
+                sign = sg;
+                const double x = log(fabs(c.v));
+                const double tt = sum + x;
+                if (fabs(sum) >= fabs(x))
+                  comp += (sum - tt) + x;
+                else
+                  comp += (x - tt) + sum;
+                sum = tt;
+                const int lab = label[l];
+                label[l] = label[m - 1];
+                label[m - 1] = lab;
+                s_swap[t] = l;
+                s_l = l;
+                s_p = c.v;
+                if (rec) {
+                  rec_pivpos[s0 + t] = l;
+                  rec_pivval[s0 + t] = c.v;
+                }
               }
             }
           }
-        }
-        __syncthreads();
-        if (s_bad) break;
-        const int l = s_l;
-        const double p = s_p;
-        // row t: factor (Eq. (3), Sec. 2.3) with the exchange of columns l and m-1
-        // applied on the fly (Sec. 2.4); the boundary keeps the pivot. Other panel
-        // rows: the exchange itself.
-        for (int j = tid; j < m - 1; j += kBT) {
-          const T v = (j == l) ? P[t * pw + m - 1] : P[t * pw + j];
-          P[t * pw + j] = (sizeof(T) == 4) ? (T)__fdiv_rn((float)v, (float)p) : (T)((double)v / p);
-          if (j == l) P[t * pw + m - 1] = (T)p;
-        }
-        if (l != m - 1) {
-          for (int i = tid; i < bb; i += kBT) {
-            if (i == t) continue;
-            const T v = P[i * pw + l];
-            P[i * pw + l] = P[i * pw + m - 1];
-            P[i * pw + m - 1] = v;
+          __syncthreads();
+          if (s_bad) break;
+          const int l = s_l;
+          const double p = s_p;
+          // row t: factor (Eq. (3), Sec. 2.3) with the exchange of columns l and m-1
+          // applied on the fly (Sec. 2.4); the boundary keeps the pivot. Other panel
+          // rows: the exchange itself.
+          for (int j = tid; j < m - 1; j += kBT) {
+            const T v = (j == l) ? P[t * pw + m - 1] : P[t * pw + j];
+            P[t * pw + j] = (sizeof(T) == 4) ? (T)__fdiv_rn((float)v, (float)p) : (T)((double)v / p);
+            if (j == l) P[t * pw + m - 1] = (T)p;
           }
+          if (l != m - 1) {
+            for (int i = tid; i < bb; i += kBT) {
+              if (i == t) continue;
+              const T v = P[i * pw + l];
+              P[i * pw + l] = P[i * pw + m - 1];
+              P[i * pw + m - 1] = v;
+            }
+          }
+          __syncthreads();
+          // rank-1 update of the remaining panel rows (Eq. (2)), one warp per row
+          for (int i = t + 1 + warp; i < bb; i += kBT / 32) {
+            const T ci = P[i * pw + m - 1];
+            for (int j = lane; j < m - 1; j += 32) P[i * pw + j] = fma_t(-ci, P[t * pw + j], P[i * pw + j]);
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        // rank-1 update of the remaining panel rows (Eq. (2)), one warp per row
-        for (int i = t + 1 + warp; i < bb; i += kBT / 32) {
-          const T ci = P[i * pw + m - 1];
-          for (int j = lane; j < m - 1; j += 32) P[i * pw + j] = fma_t(-ci, P[t * pw + j], P[i * pw + j]);
-        }
-        __syncthreads();
       }
       if (s_bad) break;
       if (rec) {
@@ -353,7 +435,16 @@ __global__ void __launch_bounds__(kBT)
       }
       __syncthreads();
     }
-    if (tid == 0) {
+    if (sizeof(T) == 4 && tid == 0) {
+      args.mflags[mat] = s_bad;
+      if (rec) {
+        RecordHeader* h = reinterpret_cast<RecordHeader*>(rec);
+        h->n = n;
+        h->ldf = ldw;
+        h->mode = args.mode;
+      }
+    }
+    if (sizeof(T) == 8 && tid == 0) {
       flags = s_bad;
       double sg, la;
       if (flags & kFlagNaN) {
@@ -383,6 +474,59 @@ __global__ void __launch_bounds__(kBT)
   }
 }
 
+// FP32 results: sign and compensated log-sum of each matrix's pivots (in pivot
+// order, the same steps as per pivot), one warp per matrix.
+__global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int count, int n_max,
+                                        const int* __restrict__ mflags, const double* __restrict__ pv,
+                                        const int* __restrict__ pp, void* const* __restrict__ factors,
+                                        double* __restrict__ signs, double* __restrict__ logabs) {
+  const int mat = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (mat >= count) return;
+  const int64_t n = n_arr[mat];
+  const double qnan = __longlong_as_double(0x7ff8000000000000ULL);
+  if (n <= 0 || n > n_max) {
+    if (lane == 0) {
+      signs[mat] = n == 0 ? 1.0 : qnan;
+      logabs[mat] = n == 0 ? 0.0 : qnan;
+    }
+    return;
+  }
+  char* rec = factors ? static_cast<char*>(factors[mat]) : nullptr;
+  const double* piv_v = pv + (int64_t)mat * n_max;
+  const int* piv_p = pp + (int64_t)mat * n_max;
+  if (rec) {
+    const size_t ldw = align_up((size_t)n, 32);
+    char* q = rec + kAlign + align_up((size_t)n * ldw * 4, kAlign);
+    q += align_up((size_t)n * 4, kAlign);  // colperm
+    piv_p = reinterpret_cast<const int*>(q);
+    q += align_up((size_t)n * 4, kAlign);
+    piv_v = reinterpret_cast<const double*>(q);
+  }
+  const int flags = mflags[mat];
+  double sign = 1.0, sum = 0.0, comp = 0.0;
+  if (flags == 0) panel_sign_logsum(piv_v, piv_p, 0, (int)n, (int)n, sign, sum, comp);
+  if (lane != 0) return;
+  double sg, la;
+  if (flags & kFlagNaN) {
+    sg = la = qnan;
+  } else if (flags & kFlagSingular) {
+    sg = 0.0;
+    la = -__longlong_as_double(0x7ff0000000000000ULL);
+  } else {
+    sg = sign;
+    la = sum + comp;
+  }
+  signs[mat] = sg;
+  logabs[mat] = la;
+  if (rec) {
+    RecordHeader* h = reinterpret_cast<RecordHeader*>(rec);
+    h->flags = flags;
+    h->sign = sg;
+    h->logabs = la;
+  }
+}
+
 template <typename T>
 ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                       const int64_t* lda, int64_t count, int64_t n_max, double* signs,
@@ -407,7 +551,12 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   per_sm = std::min(per_sm, 4);
   const int64_t grid = std::min<int64_t>((int64_t)device_sm_count() * per_sm, count);
   const size_t ws_bytes = factors ? 0 : (size_t)grid * n_max * ldw * sizeof(T);
-  const size_t aux_bytes = align_up((size_t)count * 4, kAlign) + align_up((size_t)(n_max + 2) * 4, kAlign) + kAlign;
+  const bool f32 = sizeof(T) == 4;
+  const size_t piv_bytes = (f32 && !factors) ? align_up((size_t)count * n_max * 8, kAlign) +
+                                                   align_up((size_t)count * n_max * 4, kAlign)
+                                             : 0;
+  const size_t aux_bytes = align_up((size_t)count * 4, kAlign) + align_up((size_t)(n_max + 2) * 4, kAlign) + kAlign +
+                           (f32 ? align_up((size_t)count * 4, kAlign) : 0) + piv_bytes;
   void* scratch = nullptr;
   ld_status st = scratch_alloc(&scratch, align_up(ws_bytes, kAlign) + aux_bytes + kAlign, stream);
   if (st != LD_OK) return st;
@@ -419,6 +568,19 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   int* hist = reinterpret_cast<int*>(p);
   p += align_up((size_t)(n_max + 2) * 4, kAlign);
   int* counter = reinterpret_cast<int*>(p);
+  p += kAlign;
+  int* mflags = nullptr;
+  double* pv = nullptr;
+  int* pp = nullptr;
+  if (f32) {
+    mflags = reinterpret_cast<int*>(p);
+    p += align_up((size_t)count * 4, kAlign);
+    if (!factors) {
+      pv = reinterpret_cast<double*>(p);
+      p += align_up((size_t)count * n_max * 8, kAlign);
+      pp = reinterpret_cast<int*>(p);
+    }
+  }
   {
     ProfScope ps("batched_order", stream);
     order_kernel<<<1, 1024, 0, stream>>>(n, (int)count, (int)n_max, order, counter, hist);
@@ -426,11 +588,17 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   if (st == LD_OK) {
     BatchedArgs a{A_ptrs, n,      lda,    (int)a_dtype, (int)count, (int)n_max, ldw,
-                  order,  counter, signs, logabs,       factors,    (int)mode, {}};
+                  order,  counter, signs, logabs,       factors,    (int)mode, pv, pp, mflags, {}};
     const int* kbt = tuned_batched_kb();
     for (int k = 0; k < kTuneBuckets; ++k) a.kb_table[k] = std::min(kKB, std::max(1, kbt[k]));
     ProfScope ps("batched", stream);
     batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, factors ? nullptr : ws);
+    if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+  }
+  if (st == LD_OK && f32) {
+    ProfScope ps("batched_finalize", stream);
+    batched_finalize_kernel<<<(unsigned)ceil_div(count * 32, 256), 256, 0, stream>>>(
+        n, (int)count, (int)n_max, mflags, pv, pp, factors, signs, logabs);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   scratch_free(scratch, stream);
