@@ -83,17 +83,21 @@ __device__ __forceinline__ T load_in(const void* A, int a_dtype, int64_t idx) {
                                  : static_cast<T>(static_cast<const float*>(A)[idx]);
 }
 
+// Panel row pitch in shared memory: a multiple of 4 elements (16-byte rows for
+// vector loads), offset by 4 from the size so rows start in different banks.
+__host__ __device__ inline int batched_pitch(int64_t n_max) { return (int)(((n_max + 3) & ~3) + 4); }
+
 template <typename T>
 __global__ void __launch_bounds__(kBT)
     batched_kernel(BatchedArgs args, T* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_max = args.n_max;
-  const int pw = n_max + 1;                                   // panel row pitch
+  const int pw = batched_pitch(n_max);                         // panel row pitch
   T* P = reinterpret_cast<T*>(smem_raw);                      // kKB x pw
   int* label = reinterpret_cast<int*>(P + kKB * pw);          // n_max
   int* moved_dst = label + n_max;                             // 2 kKB
   int* moved_src = moved_dst + 2 * kKB;                       // 2 kKB
-  T* Cs = reinterpret_cast<T*>(                               // kBT x (kKB + 1) multipliers
+  T* Cs = reinterpret_cast<T*>(                               // kKB x kBT multipliers (by pivot)
       (reinterpret_cast<uintptr_t>(moved_src + 2 * kKB) + 15) & ~static_cast<uintptr_t>(15));
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(kBT)
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
             if (t < bb) {
-              Cs[tid * (kKB + 1) + t] = x[t];
+              Cs[t * kBT + tid] = x[t];
               if (rec) row[m0 - 1 - t] = x[t];  // multipliers (L) of this panel
             }
           }
@@ -406,19 +410,38 @@ __global__ void __launch_bounds__(kBT)
         for (int tile = tid; tile < nrt * nct; tile += kBT) {
           const int ri = (tile / nct) * 4, cj = (tile % nct) * 4;
           T acc[4][4];
+          const bool full4 = cj + 4 <= ncols;  // a 16-byte row segment (4-element aligned)
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i) {
+            T* wr = W + (int64_t)(r0 + ri + i) * ldw + cj;
+            if constexpr (sizeof(T) == 4) {
+              if (ri + i < R && full4) {
+                const float4 v = *reinterpret_cast<const float4*>(wr);
+                acc[i][0] = v.x;
+                acc[i][1] = v.y;
+                acc[i][2] = v.z;
+                acc[i][3] = v.w;
+                continue;
+              }
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              acc[i][j] = (ri + i < R && cj + j < ncols) ? W[(int64_t)(r0 + ri + i) * ldw + cj + j] : T(0);
+            for (int j = 0; j < 4; ++j) acc[i][j] = (ri + i < R && cj + j < ncols) ? wr[j] : T(0);
+          }
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
             if (t < bb) {
               T cv[4], rv[4];
+              if constexpr (sizeof(T) == 4) {
+                const float4 c4 = *reinterpret_cast<const float4*>(Cs + t * kBT + ri);
+                const float4 r4 = *reinterpret_cast<const float4*>(P + t * pw + cj);
+                cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+                rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+              } else {
 #pragma unroll
-              for (int i = 0; i < 4; ++i) cv[i] = Cs[(ri + i) * (kKB + 1) + t];
+                for (int i = 0; i < 4; ++i) cv[i] = Cs[t * kBT + ri + i];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) rv[j] = P[t * pw + cj + j];
+                for (int j = 0; j < 4; ++j) rv[j] = P[t * pw + cj + j];
+              }
 #pragma unroll
               for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -426,10 +449,18 @@ __global__ void __launch_bounds__(kBT)
             }
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i) {
+            T* wr = W + (int64_t)(r0 + ri + i) * ldw + cj;
+            if constexpr (sizeof(T) == 4) {
+              if (ri + i < R && full4) {
+                *reinterpret_cast<float4*>(wr) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                continue;
+              }
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-              if (ri + i < R && cj + j < ncols) W[(int64_t)(r0 + ri + i) * ldw + cj + j] = acc[i][j];
+              if (ri + i < R && cj + j < ncols) wr[j] = acc[i][j];
+          }
         }
         __syncthreads();
       }
@@ -532,8 +563,8 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
                       const int64_t* lda, int64_t count, int64_t n_max, double* signs,
                       double* logabs, void* const* factors, ld_mode mode, cudaStream_t stream) {
   const int64_t ldw = (int64_t)align_up((size_t)std::max<int64_t>(n_max, 1), 4);
-  const size_t smem = (size_t)kKB * (n_max + 1) * sizeof(T) + (size_t)n_max * 4 + 4 * kKB * 4 + 16 +
-                      (size_t)kBT * (kKB + 1) * sizeof(T) + 64;
+  const size_t smem = (size_t)kKB * batched_pitch(n_max) * sizeof(T) + (size_t)n_max * 4 +
+                      4 * kKB * 4 + 16 + (size_t)kBT * kKB * sizeof(T) + 64;
   if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
   static size_t smem_set[2] = {0, 0};
   const int ti = sizeof(T) == 8;
