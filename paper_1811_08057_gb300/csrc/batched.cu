@@ -166,10 +166,8 @@ __global__ void __launch_bounds__(kBT)
       const int bb = min(kbm, n - s0);
       const int m0 = n - s0;
       // panel rows into shared memory
-      for (int e = tid; e < bb * m0; e += kBT) {
-        const int t = e / m0, j = e % m0;
-        P[t * pw + j] = W[(int64_t)(s0 + t) * ldw + j];
-      }
+      for (int t = 0; t < bb; ++t)
+        for (int j = tid; j < m0; j += kBT) P[t * pw + j] = W[(int64_t)(s0 + t) * ldw + j];
       __syncthreads();
       if constexpr (sizeof(T) == 4) {
         // FP32: column ownership (thread x owns columns x, x + kBT, ...), one CTA
@@ -329,31 +327,42 @@ __global__ void __launch_bounds__(kBT)
       }
       const int rows = n - s0 - bb;
       if (rows <= 0 && !rec) continue;
-      // compose the panel's column exchanges into a move list on <= 2 bb positions
-      if (tid == 0) {
-        int pos[2 * kKB], val[2 * kKB];
-        int np = 0;
-        for (int t = 0; t < bb; ++t) {
-          const int a = s_swap[t], b = m0 - 1 - t;
-          int ia = -1, ib = -1;
-          for (int k = 0; k < np; ++k) {
-            if (pos[k] == a) ia = k;
-            if (pos[k] == b) ib = k;
+      // compose the panel's column exchanges into a move list on <= 2 bb
+      // positions: lane k of warp 0 takes one touched position (lanes k < bb:
+      // l_k, lanes bb + k: m0-1-k; one representative per distinct position) and
+      // follows it back through the exchanges, last to first, to the position
+      // whose column it receives
+      if (warp == 0) {
+        const int sw = (lane < bb) ? s_swap[lane] : 0;
+        int pp = -1;
+        if (lane < bb)
+          pp = sw;
+        else if (lane < 2 * bb)
+          pp = m0 - 1 - (lane - bb);
+        bool rep = lane < 2 * bb;
+        int src = pp;
+        int xs[kKB];
+#pragma unroll
+        for (int t = 0; t < kKB; ++t) xs[t] = __shfl_sync(0xffffffffu, sw, t);
+#pragma unroll
+        for (int t = kKB - 1; t >= 0; --t) {
+          if (t < bb) {
+            const int x = xs[t], y = m0 - 1 - t;
+            if ((t < lane && x == pp) || (bb + t < lane && y == pp)) rep = false;
+            if (src == x)
+              src = y;
+            else if (src == y)
+              src = x;
           }
-          if (ia < 0) { pos[np] = a; val[np] = a; ia = np++; }
-          if (ib < 0) { pos[np] = b; val[np] = b; ib = np++; }
-          const int tmp = val[ia];
-          val[ia] = val[ib];
-          val[ib] = tmp;
         }
-        int k2 = 0;
-        for (int k = 0; k < np; ++k)
-          if (pos[k] != val[k]) {
-            moved_dst[k2] = pos[k];
-            moved_src[k2] = val[k];
-            ++k2;
-          }
-        s_nmoved = k2;
+        const bool moved = rep && src != pp;
+        const unsigned bm = __ballot_sync(0xffffffffu, moved);
+        if (moved) {
+          const int k = __popc(bm & ((1u << lane) - 1u));
+          moved_dst[k] = pp;
+          moved_src[k] = src;
+        }
+        if (lane == 0) s_nmoved = __popc(bm);
       }
       __syncthreads();
       const int nmoved = s_nmoved;
