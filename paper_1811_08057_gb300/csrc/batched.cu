@@ -416,25 +416,45 @@ __global__ void __launch_bounds__(kBT)
         }
         __syncthreads();
         const int nct = (ncols + 3) / 4, nrt = (R + 3) / 4;
-        for (int tile = tid; tile < nrt * nct; tile += kBT) {
+        const int ntile = nrt * nct;
+        // load of one 4 x 4 tile of the trailing rows (16-byte segments when whole)
+        auto load_tile = [&](int tile, T (&v)[4][4]) {
           const int ri = (tile / nct) * 4, cj = (tile % nct) * 4;
-          T acc[4][4];
-          const bool full4 = cj + 4 <= ncols;  // a 16-byte row segment (4-element aligned)
+          const bool full4 = cj + 4 <= ncols;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            T* wr = W + (int64_t)(r0 + ri + i) * ldw + cj;
+            const T* wr = W + (int64_t)(r0 + ri + i) * ldw + cj;
             if constexpr (sizeof(T) == 4) {
               if (ri + i < R && full4) {
-                const float4 v = *reinterpret_cast<const float4*>(wr);
-                acc[i][0] = v.x;
-                acc[i][1] = v.y;
-                acc[i][2] = v.z;
-                acc[i][3] = v.w;
+                const float4 q = *reinterpret_cast<const float4*>(wr);
+                v[i][0] = q.x;
+                v[i][1] = q.y;
+                v[i][2] = q.z;
+                v[i][3] = q.w;
                 continue;
               }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = (ri + i < R && cj + j < ncols) ? wr[j] : T(0);
+            for (int j = 0; j < 4; ++j) v[i][j] = (ri + i < R && cj + j < ncols) ? wr[j] : T(0);
+          }
+        };
+        // FP32: the next tile's loads are issued before this tile's FMAs (FP64
+        // keeps its registers for occupancy)
+        constexpr bool kPre = sizeof(T) == 4;
+        T nxt[4][4];
+        if (kPre && tid < ntile) load_tile(tid, nxt);
+        for (int tile = tid; tile < ntile; tile += kBT) {
+          const int ri = (tile / nct) * 4, cj = (tile % nct) * 4;
+          const bool full4 = cj + 4 <= ncols;
+          T acc[4][4];
+          if (kPre) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[i][j] = nxt[i][j];
+            if (tile + kBT < ntile) load_tile(tile + kBT, nxt);
+          } else {
+            load_tile(tile, acc);
           }
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
