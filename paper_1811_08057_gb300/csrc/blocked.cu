@@ -14,6 +14,10 @@
 //     to those columns);
 //  3. trailing update A22 -= C R, R = the b factored rows over the remaining
 //     columns (tensor cores for the FP32 modes, FP64 SIMT for LD_F64_BLOCKED).
+// Steps 2-3 for the next panel's rows run on a high-priority stream right after
+// the panel; for the other trailing rows on a low-priority stream, overlapping
+// the next panel (look-ahead). A batch of one size runs the same steps panel by
+// panel across the whole batch (run_blocked_batched).
 #include <stdlib.h>
 
 #include <algorithm>

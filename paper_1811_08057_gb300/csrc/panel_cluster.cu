@@ -5,10 +5,13 @@
 // of the panel rows, and inside the CTA thread x owns the positions
 // c*W + x, c*W + x + 256, ...: every value of an owned position is read and
 // written by its owner only, except where a barrier separates the accesses.
-// The panel is processed in inner blocks of KI = 16 rows held in shared memory.
+// The panel is processed in inner blocks of KI = 16 rows held in registers
+// (each thread's positions of the block's rows).
 // Per pivot row t (two CTA barriers, no cluster barrier):
 //   - each thread offers its positions of row t (max |a|, ties to the smallest
-//     original label, Sec. 2.2); warp and CTA reductions with redux.sync;
+//     original label, Sec. 2.2); warp and CTA reductions with redux.sync; each
+//     warp stages its candidate's column (and the owner the boundary column) in
+//     shared memory;
 //   - the CTA pushes its candidate, the candidate's column (KI values) and, if it
 //     owns position m-1, the boundary column into the shared memory of every CTA
 //     of the cluster with st.async, each CTA counting the bytes it receives on
@@ -29,7 +32,8 @@
 // order with one FMA each: every element sees the per-pivot sweep's exact
 // operations. The panel's composed moves for the rows outside the panel are
 // derived at the end from the change of the column labels and written to
-// `moves` for the trailing kernels.
+// `moves` for the trailing kernels. The same kernel runs batched with one-CTA
+// clusters, one matrix per cluster.
 #include <cooperative_groups.h>
 
 #include <algorithm>
