@@ -161,6 +161,21 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ rooflines
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from one ncu capture of the kernel as it stands; keyed by
+# (kernel class, workload). Reported only for the workload it was taken on.
+NCU_TRAFFIC = {
+    ("panel", "dense N=8000 f32_3xtf32"): {
+        "bytes": 3868416 + 1536,
+        "launch": "6th panel of a sweep (m0 = 7360); its declared algorithmic bytes: 67.8e6",
+        "summary": "profiles/panel_cluster_kernel_n8000.md"},
+    ("batched", "batched4096"): {
+        "bytes": 9697747000 + 10952812000,
+        "launch": "the whole batch (one launch per step)",
+        "summary": "profiles/batched_kernel_spd4096.md"},
+}
+
+
 def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
     peaks = read_peaks()
     sec = k_ms * 1e-3
@@ -349,6 +364,10 @@ def run_ours(args):
     # roofline of the dominant kernel: algorithmic work over its event time
     k_bytes, k_flops = _lib.ld_profile_work(kernel)
     roofline = make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, args.steps)
+    tr = NCU_TRAFFIC.get((kernel, f"dense N={N} {mode}"))
+    if tr:
+        roofline["traffic"] = tr["bytes"]
+        roofline["traffic_note"] = f"ncu, one launch: {tr['launch']} ({tr['summary']})"
     roofline["kernel_shares"] = shares
 
     # end to end: pinned host input -> device -> sweep -> host result, per step
@@ -475,7 +494,9 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
     if k_flop and k_ms > 0:
         ach = k_flop / (k_ms * 1e-3) / 1e12
         roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "traffic": NCU_TRAFFIC[("batched", "batched4096")]["bytes"],
+                "traffic_note": "ncu, one launch: " + NCU_TRAFFIC[("batched", "batched4096")]["launch"],
                 "peak_note": "FP32 FMA: SMs x 128 lanes x 2 flop x sampled SM clock",
                 "kernel_shares": shares}
     value = world * units / (ms * 1e-3)
