@@ -170,22 +170,39 @@ __global__ void __launch_bounds__(192, 1)
     // epilogue: D -= acc, one TMEM lane (= one output row) per thread; warp w
     // may read TMEM lanes 32 * (w % 4) .. + 31
     const int q = warp & 3;
+    constexpr int NC = C::BN / 32;  // 32-column chunks of a row
     for (int it = 0; it < ntile; ++it) {
       const int buf = it & 1, use = it >> 1;
-      const bool got = tc::mbar_wait(&accf[buf], use & 1, err);
-      __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
-      if (!__all_sync(0xffffffffu, got)) break;
-      tc::tc_fence_after();
-      const bool clean = *reinterpret_cast<volatile int*>(err) == 0;
       const int t = t_first + it, z = t / per_z, r = t % per_z;
       const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
       const int row = m0 + q * 32 + lane;
       float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
                         : D + (int64_t)z * dstride;
       float* drow = dz + (int64_t)row * ldd;
+      // whole 16-byte-aligned 32-column chunks go through registers, prefetched
+      // two chunks ahead (the first two before the accumulator is ready)
+      auto vec_ok = [&](int c) {
+        const int col0 = n0 + c * 32;
+        return row < M && col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0;
+      };
+      float4 dv[2][8];
+      auto prefetch = [&](int c, float4 (&dst)[8]) {
+        if (vec_ok(c)) {
+#pragma unroll
+          for (int v4 = 0; v4 < 8; ++v4)
+            dst[v4] = *reinterpret_cast<const float4*>(drow + n0 + c * 32 + 4 * v4);
+        }
+      };
+      prefetch(0, dv[0]);
+      prefetch(1, dv[1]);
+      const bool got = tc::mbar_wait(&accf[buf], use & 1, err);
+      __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc::tc_fence_after();
+      const bool clean = *reinterpret_cast<volatile int*>(err) == 0;
       const int nacc = nk < C::NACC ? nk : C::NACC;
-#pragma unroll 1
-      for (int c = 0; c < C::BN / 32; ++c) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
         float a[32];
         const uint32_t lane_base =
             tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::ACC_COLS + c * 32);
@@ -201,10 +218,10 @@ __global__ void __launch_bounds__(192, 1)
         }
         const int col0 = n0 + c * 32;
         if (clean && row < M) {
-          if (col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0) {
+          if (vec_ok(c)) {
 #pragma unroll
             for (int v4 = 0; v4 < 8; ++v4) {
-              float4 v = *reinterpret_cast<float4*>(drow + col0 + 4 * v4);
+              float4 v = dv[c & 1][v4];
               v.x -= a[4 * v4 + 0];
               v.y -= a[4 * v4 + 1];
               v.z -= a[4 * v4 + 2];
@@ -217,6 +234,7 @@ __global__ void __launch_bounds__(192, 1)
               if (col0 + v1 < N) drow[col0 + v1] -= a[v1];
           }
         }
+        if (c + 2 < NC) prefetch(c + 2, dv[c & 1]);
       }
       // the buffer may be overwritten by the MMAs of tile it + 2
       tc::tc_fence_before();
