@@ -88,7 +88,7 @@ __device__ __forceinline__ T load_in(const void* A, int a_dtype, int64_t idx) {
 __host__ __device__ inline int batched_pitch(int64_t n_max) { return (int)(((n_max + 3) & ~3) + 4); }
 
 template <typename T>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
     batched_kernel(BatchedArgs args, T* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_max = args.n_max;
