@@ -338,6 +338,8 @@ def run_ours(args):
     for v in shares.values():
         v["share"] = round(v["ms"] / tot, 4)
     kernel = max(shares, key=lambda k: shares[k]["ms"]) if shares else "update"
+    # the tensor-core trailing update of the same profiled sweep (its own event time)
+    tc_work = _lib.ld_profile_work("rankb_tc") if "rankb_tc" in shares else None
     clocks = ClockSampler(local)
     time.sleep(0.3)
     _lib.ld_profile_start(kernel)
@@ -368,6 +370,14 @@ def run_ours(args):
     if tr:
         roofline["traffic"] = tr["bytes"]
         roofline["traffic_note"] = f"ncu, one launch: {tr['launch']} ({tr['summary']})"
+    if kernel == "panel":
+        # the panel is a serial chain of pivots: its time per pivot is the figure to cut
+        roofline["pivot_chain"] = {"pivots_per_step": N,
+                                   "us_per_pivot": 1e3 * k_ms / args.steps / N}
+    if tc_work and kernel != "rankb_tc":
+        roofline["secondary"] = make_roofline("rankb_tc", mode, tc_work[0], tc_work[1],
+                                              shares["rankb_tc"]["ms"],
+                                              shares["rankb_tc"]["launches"], 1)
     roofline["kernel_shares"] = shares
 
     # end to end: pinned host input -> device -> sweep -> host result, per step
