@@ -87,6 +87,18 @@ __device__ __forceinline__ T load_in(const void* A, int a_dtype, int64_t idx) {
 // vector loads), offset by 4 from the size so rows start in different banks.
 __host__ __device__ inline int batched_pitch(int64_t n_max) { return (int)(((n_max + 3) & ~3) + 4); }
 
+// Column j of the first bb panel rows into dst[0 .. kKB) (16-byte aligned; rows
+// at and past bb are written as zero), every load issued before the stores.
+template <typename T>
+__device__ __forceinline__ void stage_col(const T* P, int pw, int j, int bb, float* dst) {
+  float v[kKB];
+#pragma unroll
+  for (int i = 0; i < kKB; ++i) v[i] = (i < bb) ? (float)P[i * pw + j] : 0.f;
+#pragma unroll
+  for (int i = 0; i < kKB; i += 4)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
     batched_kernel(BatchedArgs args, T* __restrict__ ws) {
@@ -105,8 +117,8 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
   // FP32 pivot search: warp candidates, their columns and the boundary column
   // (by pivot parity)
   __shared__ KCand wredk[2][kBT / 32];
-  __shared__ float wcolb[2][kBT / 32][kKB];
-  __shared__ float lcolb[2][kKB];
+  __shared__ __align__(16) float wcolb[2][kBT / 32][kKB];
+  __shared__ __align__(16) float lcolb[2][kKB];
   __shared__ int lastlab[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -181,12 +193,10 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
           kc_init(cd);
           for (int j = tid; j < m; j += kBT) kc_offer(cd, (float)P[t * pw + j], label[j], j);
           const int src = kc_warp_best(cd);
-          if (lane == src && cd.key != 0u) {
-            const int jc = kc_pos(cd);
-            for (int i = 0; i < bb; ++i) wcolb[par][warp][i] = (float)P[i * pw + jc];
-          }
+          // columns staged with all loads issued before the stores
+          if (lane == src && cd.key != 0u) stage_col(P, pw, kc_pos(cd), bb, wcolb[par][warp]);
           if ((m - 1) % kBT == tid) {
-            for (int i = 0; i < bb; ++i) lcolb[par][i] = (float)P[i * pw + m - 1];
+            stage_col(P, pw, m - 1, bb, lcolb[par]);
             lastlab[par] = label[m - 1];
           }
           if (lane == 0) wredk[par][warp] = cd;
@@ -225,13 +235,26 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
             }
           }
           // row t factored (IEEE FP32 divide), rank-1 update of the later panel
-          // rows (Eq. (2)), own columns
+          // rows (Eq. (2)), own columns; the column's loads go out together
+          float pcv[kKB];
+#pragma unroll
+          for (int i = 0; i < kKB; i += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(pc + i);
+            pcv[i] = q.x;
+            pcv[i + 1] = q.y;
+            pcv[i + 2] = q.z;
+            pcv[i + 3] = q.w;
+          }
           for (int j = tid; j < m - 1; j += kBT) {
             const float v = (j == l) ? lc[t] : (float)P[t * pw + j];
+            float pv[kKB];
+#pragma unroll
+            for (int i = 0; i < kKB; ++i) pv[i] = (i > t && i < bb) ? (float)P[i * pw + j] : 0.f;
             const float r = __fdiv_rn(v, pf);
             P[t * pw + j] = (T)r;
-            for (int i = t + 1; i < bb; ++i)
-              P[i * pw + j] = (T)fmaf(-pc[i], r, (float)P[i * pw + j]);
+#pragma unroll
+            for (int i = 0; i < kKB; ++i)
+              if (i > t && i < bb) P[i * pw + j] = (T)fmaf(-pcv[i], r, pv[i]);
           }
         }
         if (tid == 0) s_bad = bad;

@@ -38,7 +38,9 @@ struct TcCfg {
   static constexpr int STAGES = (KIND == kTF32) ? 4 : 3;
   static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
   static constexpr int NSUB = BK / KSTEP;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  // epilogue staging: one 32 x 32 FP32 block per epilogue warp
+  static constexpr int STG_BYTES = 4 * 32 * 32 * 4;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BYTES;
   // K-chunks rotate over NACC accumulators (NACC x BN TMEM columns), summed in
   // FP32 in the epilogue: each tensor-core accumulation chain is NACC times
   // shorter. Two such buffers fill the SM's 512 TMEM columns.
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* acce = accf + 2;           // [2] accumulator buffer drained (epilogue -> MMA)
   uint64_t* done = acce + 2;           // every MMA issued has completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* stg = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tn = (N + C::BN - 1) / C::BN, tm = (M + C::BM - 1) / C::BM;
@@ -167,10 +170,17 @@ __global__ void __launch_bounds__(192, 1)
     tc::mma_commit(done);
     tc::mbar_wait(done, 0, err);
   } else if (warp >= 2) {
-    // epilogue: D -= acc, one TMEM lane (= one output row) per thread; warp w
-    // may read TMEM lanes 32 * (w % 4) .. + 31
+    // epilogue: D -= acc. Warp w may read TMEM lanes 32 * (w % 4) .. + 31 (one
+    // output row per lane). A whole 32 x 32 block (rows in range, columns inside
+    // N, 16-byte-aligned rows) goes through the warp's shared-memory block so that
+    // D is read and written by rows: lane L covers row 4j + L / 8, columns
+    // 4 (L % 8) .. + 3 of the block in pass j (128 contiguous bytes per row). Its
+    // D values are prefetched two blocks ahead (the first two before the
+    // accumulator is ready). Other blocks: per-row scalar updates.
     const int q = warp & 3;
-    constexpr int NC = C::BN / 32;  // 32-column chunks of a row
+    constexpr int NC = C::BN / 32;  // 32-column blocks of a tile row
+    float* sw = stg + q * 32 * 32;  // 16-byte chunks XOR-swizzled by row
+    const int rsub = lane >> 3, ksub = lane & 7;
     for (int it = 0; it < ntile; ++it) {
       const int buf = it & 1, use = it >> 1;
       const int t = t_first + it, z = t / per_z, r = t % per_z;
@@ -179,18 +189,16 @@ __global__ void __launch_bounds__(192, 1)
       float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
                         : D + (int64_t)z * dstride;
       float* drow = dz + (int64_t)row * ldd;
-      // whole 16-byte-aligned 32-column chunks go through registers, prefetched
-      // two chunks ahead (the first two before the accumulator is ready)
-      auto vec_ok = [&](int c) {
-        const int col0 = n0 + c * 32;
-        return row < M && col0 + 32 <= N && (reinterpret_cast<uintptr_t>(drow + col0) & 15) == 0;
-      };
+      const bool rows_ok = m0 + q * 32 + 32 <= M &&
+                           ((reinterpret_cast<uintptr_t>(dz) | (uintptr_t)(ldd * 4)) & 15) == 0;
+      float* dblk = dz + (int64_t)(m0 + q * 32 + rsub) * ldd + n0 + 4 * ksub;
+      auto whole = [&](int c) { return rows_ok && n0 + c * 32 + 32 <= N; };
       float4 dv[2][8];
       auto prefetch = [&](int c, float4 (&dst)[8]) {
-        if (vec_ok(c)) {
+        if (whole(c)) {
 #pragma unroll
-          for (int v4 = 0; v4 < 8; ++v4)
-            dst[v4] = *reinterpret_cast<const float4*>(drow + n0 + c * 32 + 4 * v4);
+          for (int j = 0; j < 8; ++j)
+            dst[j] = *reinterpret_cast<const float4*>(dblk + (int64_t)(4 * j) * ldd + c * 32);
         }
       };
       prefetch(0, dv[0]);
@@ -199,7 +207,8 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
       if (!__all_sync(0xffffffffu, got)) break;
       tc::tc_fence_after();
-      const bool clean = *reinterpret_cast<volatile int*>(err) == 0;
+      // one decision per warp (the staged path synchronises the warp)
+      const bool clean = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(err) == 0, 0);
       const int nacc = nk < C::NACC ? nk : C::NACC;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -217,18 +226,26 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
         const int col0 = n0 + c * 32;
-        if (clean && row < M) {
-          if (vec_ok(c)) {
+        if (clean) {
+          if (whole(c)) {
 #pragma unroll
-            for (int v4 = 0; v4 < 8; ++v4) {
-              float4 v = dv[c & 1][v4];
-              v.x -= a[4 * v4 + 0];
-              v.y -= a[4 * v4 + 1];
-              v.z -= a[4 * v4 + 2];
-              v.w -= a[4 * v4 + 3];
-              *reinterpret_cast<float4*>(drow + col0 + 4 * v4) = v;
+            for (int k = 0; k < 8; ++k)
+              *reinterpret_cast<float4*>(sw + lane * 32 + 4 * (k ^ (lane & 7))) =
+                  make_float4(a[4 * k + 0], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int rr = 4 * j + rsub;
+              const float4 s4 = *reinterpret_cast<const float4*>(sw + rr * 32 + 4 * (ksub ^ (rr & 7)));
+              float4 v = dv[c & 1][j];
+              v.x -= s4.x;
+              v.y -= s4.y;
+              v.z -= s4.z;
+              v.w -= s4.w;
+              *reinterpret_cast<float4*>(dblk + (int64_t)(4 * j) * ldd + c * 32) = v;
             }
-          } else {
+            __syncwarp();  // the block is rewritten by the next chunk
+          } else if (row < M) {
 #pragma unroll
             for (int v1 = 0; v1 < 32; ++v1)
               if (col0 + v1 < N) drow[col0 + v1] -= a[v1];

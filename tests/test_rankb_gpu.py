@@ -42,17 +42,20 @@ def test_rankb_update_matches_fp64(mode, shape):
     assert err <= tol, f"{mode} {shape}: {err:.3e} > {tol:.1e}"
 
 
-def test_rankb_strided_leading_dims():
-    """Leading dimensions larger than the logical widths (views into bigger buffers)."""
+@pytest.mark.parametrize("pad", [12, 10, 42])
+def test_rankb_strided_leading_dims(pad):
+    """Leading dimensions larger than the logical widths (views into bigger buffers):
+    D rows 16-byte aligned (pad 10, 42) or not (pad 12), with whole and partial
+    32 x 32 output blocks."""
     M, N, K = 200, 150, 64
-    g = torch.Generator().manual_seed(5)
+    g = torch.Generator().manual_seed(5 + pad)
     A = torch.randn(M, K + 64, generator=g)
     B = torch.randn(N, K + 128, generator=g)
-    D = torch.randn(M, N + 12, generator=g)
+    D = torch.randn(M, N + pad, generator=g)
     want = D[:, :N].double() - A[:, :K].double() @ B[:, :K].double().T
     Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()
     rc = _lib.ld_rankb_update(4, M, N, K, Ad.data_ptr(), K + 64, Bd.data_ptr(), K + 128,
-                              Dd.data_ptr(), N + 12, torch.cuda.current_stream().cuda_stream)
+                              Dd.data_ptr(), N + pad, torch.cuda.current_stream().cuda_stream)
     assert rc == 0
     got = Dd.cpu()
     assert torch.equal(got[:, N:], D[:, N:]), "columns beyond N were touched"
