@@ -100,7 +100,7 @@ __device__ __forceinline__ void stage_col(const T* P, int pw, int j, int bb, flo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
     batched_kernel(BatchedArgs args, T* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_max = args.n_max;
@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
   __shared__ int s_swap[kKB];
+  // per panel: where pivot t's column (position m0-1-t after the exchanges)
+  // started, and the trailing positions (< m0-bb) that receive a column
+  __shared__ int s_xsrc[kKB], s_odst[kKB], s_osrc[kKB], s_nout;
   // FP32 pivot search: warp candidates, their columns and the boundary column
   // (by pivot parity)
   __shared__ KCand wredk[2][kBT / 32];
@@ -163,10 +166,20 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
     }
     double* piv_v = rec ? rec_pivval : (args.pv ? args.pv + (int64_t)mat * n_max : nullptr);
     int* piv_p = rec ? rec_pivpos : (args.pp ? args.pp + (int64_t)mat * n_max : nullptr);
-    // stage the matrix into the CTA's workspace (a0)
-    for (int i = warp; i < n; i += kBT / 32)
-      for (int j = lane; j < n; j += 32)
-        W[(int64_t)i * ldw + j] = load_in<T>(A, args.a_dtype, (int64_t)i * lda + j);
+    // stage the matrix into the CTA's workspace (a0): a warp per row, eight
+    // elements per lane in flight (the loads issued before the stores)
+    for (int i = warp; i < n; i += kBT / 32) {
+      const int64_t ia = (int64_t)i * lda, iw = (int64_t)i * ldw;
+      for (int j0 = lane; j0 < n; j0 += 256) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[u] = (j0 + 32 * u < n) ? load_in<T>(A, args.a_dtype, ia + j0 + 32 * u) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + 32 * u < n) W[iw + j0 + 32 * u] = v[u];
+      }
+    }
     for (int j = tid; j < n; j += kBT) label[j] = j;
     const int kbm = args.kb_table[min(n / 64, kTuneBuckets - 1)];  // this matrix's panel depth
     double sign = 1.0, sum = 0.0, comp = 0.0;  // meaningful in thread 0
@@ -177,9 +190,16 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
     for (int s0 = 0; s0 < n; s0 += kbm) {
       const int bb = min(kbm, n - s0);
       const int m0 = n - s0;
-      // panel rows into shared memory
-      for (int t = 0; t < bb; ++t)
-        for (int j = tid; j < m0; j += kBT) P[t * pw + j] = W[(int64_t)(s0 + t) * ldw + j];
+      // panel rows into shared memory (a thread's column of the panel: loads
+      // issued before the stores)
+      for (int j = tid; j < m0; j += kBT) {
+        T v[kKB];
+#pragma unroll
+        for (int t = 0; t < kKB; ++t) v[t] = (t < bb) ? W[(int64_t)(s0 + t) * ldw + j] : T(0);
+#pragma unroll
+        for (int t = 0; t < kKB; ++t)
+          if (t < bb) P[t * pw + j] = v[t];
+      }
       __syncthreads();
       if constexpr (sizeof(T) == 4) {
         // FP32: column ownership (thread x owns columns x, x + kBT, ...), one CTA
@@ -386,6 +406,21 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
           moved_src[k] = src;
         }
         if (lane == 0) s_nmoved = __popc(bm);
+        // the same moves split by destination: inside the pivot block (the
+        // multipliers' sources) or before it (trailing columns; their sources
+        // lie in the block: an exchange fills a trailing position from the
+        // boundary, whose content always comes from the block)
+        const int pbw = m0 - bb;
+        if (lane < bb) s_xsrc[lane] = m0 - 1 - lane;
+        __syncwarp();
+        if (moved && pp >= pbw) s_xsrc[m0 - 1 - pp] = src;
+        const unsigned om = __ballot_sync(0xffffffffu, moved && pp < pbw);
+        if (moved && pp < pbw) {
+          const int k = __popc(om & ((1u << lane) - 1u));
+          s_odst[k] = pp;
+          s_osrc[k] = src;
+        }
+        if (lane == 0) s_nout = __popc(om);
       }
       __syncthreads();
       const int nmoved = s_nmoved;
@@ -411,16 +446,43 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 4 : 1)
         const int R = min(kBT, n - r0);
         if (tid < R) {
           T* row = W + (int64_t)(r0 + tid) * ldw;
-          T mv[2 * kKB];
+          const int pb = m0 - bb;  // first position of the panel's pivot block
+          const bool vec4 = sizeof(T) == 4 && bb == kKB && (pb & 3) == 0 && (ldw & 3) == 0 &&
+                            (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+          // the row's pivot block (positions pb .. m0-1, the old layout) into this
+          // thread's column of Cs: one 64-byte read where it is whole and aligned
+          if (vec4) {
 #pragma unroll
-          for (int k = 0; k < 2 * kKB; ++k)
-            if (k < nmoved) mv[k] = row[moved_src[k]];
+            for (int i = 0; i < kKB; i += 4) {
+              const float4 q = *reinterpret_cast<const float4*>(row + pb + i);
+              Cs[(i + 0) * kBT + tid] = q.x;
+              Cs[(i + 1) * kBT + tid] = q.y;
+              Cs[(i + 2) * kBT + tid] = q.z;
+              Cs[(i + 3) * kBT + tid] = q.w;
+            }
+          } else {
 #pragma unroll
-          for (int k = 0; k < 2 * kKB; ++k)
-            if (k < nmoved) row[moved_dst[k]] = mv[k];
+            for (int i = 0; i < kKB; ++i)
+              if (i < bb) Cs[i * kBT + tid] = row[pb + i];
+          }
+          // the panel's column moves (new[dst] = old[src]), reading old values
+          // only: the multipliers (pivot t's column ends at m0-1-t) from the
+          // block or the row, then the trailing positions that receive a column
           T x[kKB];
 #pragma unroll
-          for (int t = 0; t < kKB; ++t) x[t] = (t < bb) ? row[m0 - 1 - t] : T(0);
+          for (int t = 0; t < kKB; ++t) {
+            x[t] = T(0);
+            if (t < bb) {
+              const int xs = s_xsrc[t];
+              x[t] = (xs >= pb) ? Cs[(xs - pb) * kBT + tid] : row[xs];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kKB; ++k)
+            if (k < s_nout) {
+              const int os = s_osrc[k];
+              row[s_odst[k]] = (os >= pb) ? Cs[(os - pb) * kBT + tid] : row[os];
+            }
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
             if (t < bb) {
