@@ -87,6 +87,21 @@ __device__ __forceinline__ T load_in(const void* A, int a_dtype, int64_t idx) {
 // vector loads), offset by 4 from the size so rows start in different banks.
 __host__ __device__ inline int batched_pitch(int64_t n_max) { return (int)(((n_max + 3) & ~3) + 4); }
 
+// Column j of a full panel at pivot TT: row TT factored (IEEE FP32 divide by the
+// pivot pf, Eq. (3)), rows TT+1 .. kKB-1 updated (Eq. (2)); the column's loads go
+// out before the divide.
+template <int TT>
+__device__ __forceinline__ void panel_col_step(float* P, int pw, int j, float v, float pf,
+                                               const float (&pcv)[kKB]) {
+  float pv[kKB];
+#pragma unroll
+  for (int i = TT + 1; i < kKB; ++i) pv[i] = P[i * pw + j];
+  const float r = __fdiv_rn(v, pf);
+  P[TT * pw + j] = r;
+#pragma unroll
+  for (int i = TT + 1; i < kKB; ++i) P[i * pw + j] = fmaf(-pcv[i], r, pv[i]);
+}
+
 // Column j of the first bb panel rows into dst[0 .. kKB) (16-byte aligned; rows
 // at and past bb are written as zero), every load issued before the stores.
 template <typename T>
@@ -267,6 +282,22 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           }
           for (int j = tid; j < m - 1; j += kBT) {
             const float v = (j == l) ? lc[t] : (float)P[t * pw + j];
+            if (bb == kKB) {  // a full panel: pivot index and row range known statically
+              switch (t) {
+#define LD_PANEL_COL(TT)                                  \
+  case TT:                                                \
+    panel_col_step<TT>(P, pw, j, v, pf, pcv);             \
+    break;
+                LD_PANEL_COL(0) LD_PANEL_COL(1) LD_PANEL_COL(2) LD_PANEL_COL(3)
+                LD_PANEL_COL(4) LD_PANEL_COL(5) LD_PANEL_COL(6) LD_PANEL_COL(7)
+                LD_PANEL_COL(8) LD_PANEL_COL(9) LD_PANEL_COL(10) LD_PANEL_COL(11)
+                LD_PANEL_COL(12) LD_PANEL_COL(13) LD_PANEL_COL(14) LD_PANEL_COL(15)
+#undef LD_PANEL_COL
+                default:
+                  break;
+              }
+              continue;
+            }
             float pv[kKB];
 #pragma unroll
             for (int i = 0; i < kKB; ++i) pv[i] = (i > t && i < bb) ? (float)P[i * pw + j] : 0.f;
@@ -619,28 +650,15 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
   }
 }
 
-// FP32 results: sign and compensated log-sum of each matrix's pivots (in pivot
-// order, the same steps as per pivot), one warp per matrix.
-__global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int count, int n_max,
-                                        const int* __restrict__ mflags, const double* __restrict__ pv,
-                                        const int* __restrict__ pp, void* const* __restrict__ factors,
-                                        double* __restrict__ signs, double* __restrict__ logabs) {
-  const int mat = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (mat >= count) return;
-  const int64_t n = n_arr[mat];
-  const double qnan = __longlong_as_double(0x7ff8000000000000ULL);
-  if (n <= 0 || n > n_max) {
-    if (lane == 0) {
-      signs[mat] = n == 0 ? 1.0 : qnan;
-      logabs[mat] = n == 0 ? 0.0 : qnan;
-    }
-    return;
-  }
-  char* rec = factors ? static_cast<char*>(factors[mat]) : nullptr;
-  const double* piv_v = pv + (int64_t)mat * n_max;
-  const int* piv_p = pp + (int64_t)mat * n_max;
-  if (rec) {
+// Pivot record of matrix `mat`: FP64 pivot values and positions (in its factor
+// record when there is one, else in the per-matrix scratch rows).
+__device__ __forceinline__ void batched_pivots(int mat, int64_t n, int n_max, const double* pv,
+                                               const int* pp, void* const* factors,
+                                               const double*& piv_v, const int*& piv_p) {
+  piv_v = pv + (int64_t)mat * n_max;
+  piv_p = pp + (int64_t)mat * n_max;
+  if (factors) {
+    char* rec = static_cast<char*>(factors[mat]);
     const size_t ldw = align_up((size_t)n, 32);
     char* q = rec + kAlign + align_up((size_t)n * ldw * 4, kAlign);
     q += align_up((size_t)n * 4, kAlign);  // colperm
@@ -648,10 +666,68 @@ __global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int c
     q += align_up((size_t)n * 4, kAlign);
     piv_v = reinterpret_cast<const double*>(q);
   }
+}
+
+// log|p| of every pivot of every matrix (one thread per pivot slot), into
+// xlog[mat * n_max + t].
+__global__ void batched_logs_kernel(const int64_t* __restrict__ n_arr, int count, int n_max,
+                                    const int* __restrict__ mflags, const double* __restrict__ pv,
+                                    const int* __restrict__ pp, void* const* __restrict__ factors,
+                                    double* __restrict__ xlog) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)count * n_max) return;
+  const int mat = (int)(idx / n_max), t = (int)(idx % n_max);
+  const int64_t n = n_arr[mat];
+  if (n <= 0 || n > n_max || t >= n || mflags[mat] != 0) return;
+  const double* piv_v;
+  const int* piv_p;
+  batched_pivots(mat, n, n_max, pv, pp, factors, piv_v, piv_p);
+  xlog[idx] = log(fabs(piv_v[t]));
+}
+
+// FP32 results: sign and compensated log-sum of each matrix's pivots, in pivot
+// order (the same FP64 steps as a per-pivot accumulation, on the logs of
+// batched_logs_kernel). One thread per matrix, matrices taken in the size order
+// of `order` so that the lanes of a warp carry similar pivot counts.
+__global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int count, int n_max,
+                                        const int* __restrict__ order,
+                                        const int* __restrict__ mflags, const double* __restrict__ pv,
+                                        const int* __restrict__ pp, void* const* __restrict__ factors,
+                                        const double* __restrict__ xlog,
+                                        double* __restrict__ signs, double* __restrict__ logabs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const int mat = order[q];
+  const int64_t n = n_arr[mat];
+  const double qnan = __longlong_as_double(0x7ff8000000000000ULL);
+  if (n <= 0 || n > n_max) {
+    signs[mat] = n == 0 ? 1.0 : qnan;
+    logabs[mat] = n == 0 ? 0.0 : qnan;
+    return;
+  }
+  char* rec = factors ? static_cast<char*>(factors[mat]) : nullptr;
+  const double* piv_v;
+  const int* piv_p;
+  batched_pivots(mat, n, n_max, pv, pp, factors, piv_v, piv_p);
+  const double* xm = xlog + (int64_t)mat * n_max;
   const int flags = mflags[mat];
-  double sign = 1.0, sum = 0.0, comp = 0.0;
-  if (flags == 0) panel_sign_logsum(piv_v, piv_p, 0, (int)n, (int)n, sign, sum, comp);
-  if (lane != 0) return;
+  double sum = 0.0, comp = 0.0;
+  int odd = 0;
+  if (flags == 0) {
+#pragma unroll 8
+    for (int t = 0; t < (int)n; ++t) {
+      const double v = piv_v[t];
+      const int l = piv_p[t];
+      const int m = (int)n - t;
+      // sgn(p), the Laplace sign (-1)^(1+m) and the exchange of l and m-1
+      odd ^= ((v < 0.0) + ((m + 1) & 1) + (l != m - 1)) & 1;
+      const double x = xm[t];
+      const double s2 = sum + x;
+      const double e = (fabs(sum) >= fabs(x)) ? (sum - s2) + x : (x - s2) + sum;
+      comp += e;
+      sum = s2;
+    }
+  }
   double sg, la;
   if (flags & kFlagNaN) {
     sg = la = qnan;
@@ -659,7 +735,7 @@ __global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int c
     sg = 0.0;
     la = -__longlong_as_double(0x7ff0000000000000ULL);
   } else {
-    sg = sign;
+    sg = odd ? -1.0 : 1.0;
     la = sum + comp;
   }
   signs[mat] = sg;
@@ -700,8 +776,9 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   const size_t piv_bytes = (f32 && !factors) ? align_up((size_t)count * n_max * 8, kAlign) +
                                                    align_up((size_t)count * n_max * 4, kAlign)
                                              : 0;
+  const size_t xlog_bytes = f32 ? align_up((size_t)count * n_max * 8, kAlign) : 0;
   const size_t aux_bytes = align_up((size_t)count * 4, kAlign) + align_up((size_t)(n_max + 2) * 4, kAlign) + kAlign +
-                           (f32 ? align_up((size_t)count * 4, kAlign) : 0) + piv_bytes;
+                           (f32 ? align_up((size_t)count * 4, kAlign) : 0) + piv_bytes + xlog_bytes;
   void* scratch = nullptr;
   ld_status st = scratch_alloc(&scratch, align_up(ws_bytes, kAlign) + aux_bytes + kAlign, stream);
   if (st != LD_OK) return st;
@@ -717,9 +794,12 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   int* mflags = nullptr;
   double* pv = nullptr;
   int* pp = nullptr;
+  double* xlog = nullptr;
   if (f32) {
     mflags = reinterpret_cast<int*>(p);
     p += align_up((size_t)count * 4, kAlign);
+    xlog = reinterpret_cast<double*>(p);
+    p += xlog_bytes;
     if (!factors) {
       pv = reinterpret_cast<double*>(p);
       p += align_up((size_t)count * n_max * 8, kAlign);
@@ -741,9 +821,16 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   if (st == LD_OK && f32) {
+    {
+      ProfScope ps("batched_logs", stream);
+      batched_logs_kernel<<<(unsigned)ceil_div(count * n_max, 256), 256, 0, stream>>>(
+          n, (int)count, (int)n_max, mflags, pv, pp, factors, xlog);
+    }
+    if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
+    // one warp per CTA: the serial sums spread over the SMs
     ProfScope ps("batched_finalize", stream);
-    batched_finalize_kernel<<<(unsigned)ceil_div(count * 32, 256), 256, 0, stream>>>(
-        n, (int)count, (int)n_max, mflags, pv, pp, factors, signs, logabs);
+    batched_finalize_kernel<<<(unsigned)ceil_div(count, 32), 32, 0, stream>>>(
+        n, (int)count, (int)n_max, order, mflags, pv, pp, factors, xlog, signs, logabs);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   scratch_free(scratch, stream);
