@@ -23,6 +23,7 @@ namespace ld {
 namespace {
 
 constexpr int kNB = 128;  // block size of the backward sweep
+constexpr int kRPW = 4;   // rows per warp in the triangular block solves
 
 // Natural-order L and U of one record: L[i][c] = F[i][n-1-c] for c <= i,
 // U[i][c] = F[i][n-1-c] for c > i, U[i][i] = 1; identity in the padding.
@@ -92,34 +93,35 @@ __global__ void __launch_bounds__(256, 2)
   const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)z * np * np;
   constexpr int KQ = kNB / 32;
-  for (int r = 2 * (blockIdx.x * 8 + (threadIdx.x >> 5)); r < M; r += gridDim.x * 16) {
-    const bool two = r + 1 < M;
-    T* row0 = Yv + base + (int64_t)r * np + c0;
-    T* row1 = two ? row0 + np : row0;
-    T x[KQ], y[KQ];
+  // kRPW rows per warp share each step's shuffles and triangular-factor loads
+  for (int r = kRPW * (blockIdx.x * 8 + (threadIdx.x >> 5)); r < M; r += gridDim.x * 8 * kRPW) {
+    T x[kRPW][KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      x[q] = row0[lane + 32 * q];
-      y[q] = row1[lane + 32 * q];
+    for (int w = 0; w < kRPW; ++w) {
+      const T* rw = Yv + base + (int64_t)min(r + w, M - 1) * np + c0;
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) x[w][q] = rw[lane + 32 * q];
     }
     if (LOWER) {
 #pragma unroll
       for (int qq = 0; qq < KQ; ++qq) {
+#pragma unroll
         for (int tt = 0; tt < 32; ++tt) {
           const int k = qq * 32 + tt;
           if (lane == tt) {
-            x[qq] = x[qq] * rdiag[k];
-            y[qq] = y[qq] * rdiag[k];
+#pragma unroll
+            for (int w = 0; w < kRPW; ++w) x[w][qq] = x[w][qq] * rdiag[k];
           }
-          const T xk = __shfl_sync(0xffffffffu, x[qq], tt);
-          const T yk = __shfl_sync(0xffffffffu, y[qq], tt);
+          T xk[kRPW];
+#pragma unroll
+          for (int w = 0; w < kRPW; ++w) xk[w] = __shfl_sync(0xffffffffu, x[w][qq], tt);
 #pragma unroll
           for (int q = qq; q < KQ; ++q) {
             const int m = lane + 32 * q;
             if (m > k) {
               const T smk = S[m][k];
-              x[q] = fma_t(-smk, xk, x[q]);
-              y[q] = fma_t(-smk, yk, y[q]);
+#pragma unroll
+              for (int w = 0; w < kRPW; ++w) x[w][q] = fma_t(-smk, xk[w], x[w][q]);
             }
           }
         }
@@ -127,36 +129,37 @@ __global__ void __launch_bounds__(256, 2)
     } else {
 #pragma unroll
       for (int qq = KQ - 1; qq >= 0; --qq) {
+#pragma unroll
         for (int tt = 31; tt >= 0; --tt) {
           const int k = qq * 32 + tt;
-          const T xk = __shfl_sync(0xffffffffu, x[qq], tt);
-          const T yk = __shfl_sync(0xffffffffu, y[qq], tt);
+          T xk[kRPW];
+#pragma unroll
+          for (int w = 0; w < kRPW; ++w) xk[w] = __shfl_sync(0xffffffffu, x[w][qq], tt);
 #pragma unroll
           for (int q = 0; q <= qq; ++q) {
             const int m = lane + 32 * q;
             if (m < k) {
               const T smk = S[m][k];
-              x[q] = fma_t(-smk, xk, x[q]);
-              y[q] = fma_t(-smk, yk, y[q]);
+#pragma unroll
+              for (int w = 0; w < kRPW; ++w) x[w][q] = fma_t(-smk, xk[w], x[w][q]);
             }
           }
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      const int idx = lane + 32 * q;
-      row0[idx] = x[q];
-      if (two) row1[idx] = y[q];
-      if constexpr (SPLIT) {
-        float h, lo;
-        tf32_split((float)x[q], h, lo);
-        Yh[base + (int64_t)r * np + c0 + idx] = h;
-        Yl[base + (int64_t)r * np + c0 + idx] = lo;
-        if (two) {
-          tf32_split((float)y[q], h, lo);
-          Yh[base + (int64_t)(r + 1) * np + c0 + idx] = h;
-          Yl[base + (int64_t)(r + 1) * np + c0 + idx] = lo;
+    for (int w = 0; w < kRPW; ++w) {
+      if (r + w >= M) break;
+      T* rw = Yv + base + (int64_t)(r + w) * np + c0;
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const int idx = lane + 32 * q;
+        rw[idx] = x[w][q];
+        if constexpr (SPLIT) {
+          float h, lo;
+          tf32_split((float)x[w][q], h, lo);
+          Yh[base + (int64_t)(r + w) * np + c0 + idx] = h;
+          Yl[base + (int64_t)(r + w) * np + c0 + idx] = lo;
         }
       }
     }
