@@ -672,8 +672,10 @@ ld_status run_blocked_batched(const void* const* A_ptrs, ld_dtype a_dtype, const
   }
   if (st == LD_OK) {
     ProfScope ps("finalize", stream);
-    finalize_batched_kernel<<<(unsigned)ceil_div(count * 32, 256), 256, 0, stream>>>(
-        recs, ro, (int)n, (int)count, err, signs, logabs);
+    // one warp per CTA: the serial FP64 sums of different matrices land on
+    // different SMs' FP64 pipes
+    finalize_batched_kernel<<<(unsigned)count, 32, 0, stream>>>(recs, ro, (int)n, (int)count, err,
+                                                                 signs, logabs);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   scratch_free(scratch, stream);
