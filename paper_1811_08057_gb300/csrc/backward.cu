@@ -291,8 +291,8 @@ ld_status run_backward(const void* const* recs, void* const* grads, const double
     return LD_ERR_CUDA;
   }
   auto solve = [&](int I, int64_t M, bool lower) -> ld_status {
-    // >= 128 rows per block amortise staging the 128 x 128 triangular block
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M, 128), 8)), (unsigned)count);
+    // >= 256 rows per block amortise staging the 128 x 128 triangular block
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M, 256), 4)), (unsigned)count);
     ProfScope ps("bwd_rowsolve", stream, (double)count * M * kNB * sizeof(T) * (SPLIT ? 4.0 : 2.0),
                  (double)count * M * kNB * kNB);
     if (lower)
