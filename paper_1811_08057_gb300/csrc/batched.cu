@@ -3,7 +3,7 @@
 //
 // Each CTA takes matrices from a queue ordered by decreasing size (longest
 // processing time first) and runs the whole sweep of one matrix by itself:
-//   - the matrix is copied into a per-CTA workspace (global memory, L2-resident);
+//   - the matrix is copied into a per-CTA workspace (global memory);
 //   - panels of KB pivot rows live in shared memory; for each pivot row: max-abs
 //     column search (Sec. 2.2), exchange of the pivot column with the boundary
 //     column (Sec. 2.4), row factoring with an IEEE divide (Eq. (3)), rank-1
@@ -14,6 +14,9 @@
 //     register. Every element therefore sees exactly the plain sweep's sequence
 //     of operations (bit-identical results), while the trailing rows are read and
 //     written once per panel instead of once per pivot.
+// FP32 storage defers the sign and the compensated log-sum: the pivots are
+// recorded, batched_logs_kernel takes all their logs at once and
+// batched_finalize_kernel adds them per matrix in pivot order.
 #include <algorithm>
 
 #include "profile.cuh"
