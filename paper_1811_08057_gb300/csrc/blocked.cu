@@ -152,21 +152,24 @@ __global__ void __launch_bounds__(256, 3)
     a[k] = (t < bb) ? row0[m0 - 1 - t] : T(0);
     b[k] = (t < bb) ? row1[m0 - 1 - t] : T(0);
   }
+  // (steps unrolled: the factor loads of later steps go out ahead of the chain)
 #pragma unroll
   for (int kk = 0; kk < KMAX; ++kk) {
     if (kk * 32 < bb) {
+#pragma unroll
       for (int tt = 0; tt < 32; ++tt) {
         const int t = kk * 32 + tt;
-        if (t >= bb) break;
-        const T ca = __shfl_sync(0xffffffffu, a[kk], tt);
-        const T cb = __shfl_sync(0xffffffffu, b[kk], tt);
+        if (t < bb) {
+          const T ca = __shfl_sync(0xffffffffu, a[kk], tt);
+          const T cb = __shfl_sync(0xffffffffu, b[kk], tt);
 #pragma unroll
-        for (int k = kk; k < KMAX; ++k) {
-          const int t2 = lane + 32 * k;
-          if (t2 > t && t2 < bb) {
-            const T u = U[t * bb + t2];
-            a[k] = fma_t(-ca, u, a[k]);
-            b[k] = fma_t(-cb, u, b[k]);
+          for (int k = kk; k < KMAX; ++k) {
+            const int t2 = lane + 32 * k;
+            if (t2 > t && t2 < bb) {
+              const T u = U[t * bb + t2];
+              a[k] = fma_t(-ca, u, a[k]);
+              b[k] = fma_t(-cb, u, b[k]);
+            }
           }
         }
       }
