@@ -486,15 +486,25 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
     _lib.ld_profile_start(kernel)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # under torchrun every rank sweeps its own batch (weak scaling, no collective
+    # on the data path); the job's time is the slowest rank's
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
     _lib.ld_profile_stop()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tm = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm[0])
     launches_all, _ = _lib.ld_profile_query(None)
     k_launches, k_ms = _lib.ld_profile_query(kernel)
     peaks = read_peaks()
@@ -530,6 +540,8 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
             "e2e": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
