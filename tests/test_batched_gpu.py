@@ -122,3 +122,43 @@ def test_batched_config_4096_sampled():
     for i in rng.choice(4096, size=24, replace=False):
         ref = oracle.logdet(dev[i].double().cpu().numpy())
         assert rel_err(float(l[i]), ref.logabs) <= 1e-5, (i, sizes[i])
+
+
+def test_batched_f32_bitwise_equals_single():
+    """FP32 storage: the batched kernel (column moves from the pivot block, rank-1
+    updates per element in pivot order, deferred ordered log-sums) against the
+    plain FP32 sweep, bit for bit, with sizes past 512 (three and four columns
+    per thread, several trailing-row chunks)."""
+    rng = np.random.default_rng(5)
+    sizes = [int(x) for x in rng.integers(1, 1000, size=12)] + [513, 768, 999]
+    mats = [workloads.dense_gaussian(n, seed=200 + n) for n in sizes]
+    dev = [torch.from_numpy(A).float().cuda() for A in mats]
+    s, l = api.logdet_batched(dev, "f32_plain")
+    for i, A in enumerate(dev):
+        ss, ll = api.logdet(A, "f32_plain")
+        assert float(s[i]) == float(ss), (i, sizes[i])
+        assert float(l[i]) == float(ll), (i, sizes[i], float(l[i]), float(ll))
+
+
+def test_batched_f32_edge_cases():
+    """The deferred FP32 results: all-zero pivot row, NaN, empty matrix and a size
+    above the declared bound, each confined to its own matrix."""
+    A = torch.from_numpy(workloads.dense_gaussian(40, seed=1)).float().cuda()
+    Z = A.clone()
+    Z[10] = 0
+    N = A.clone()
+    N[5, 5] = float("nan")
+    E = torch.zeros(0, 0, dtype=torch.float32, device="cuda")
+    s, l = api.logdet_batched([A, Z, N, E, A], "f32_plain")
+    ss, ll = api.logdet(A, "f32_plain")
+    for i in (0, 4):
+        assert float(s[i]) == float(ss) and float(l[i]) == float(ll)
+    assert float(s[1]) == 0.0 and float(l[1]) == -math.inf
+    assert math.isnan(float(s[2])) and math.isnan(float(l[2]))
+    assert float(s[3]) == 1.0 and float(l[3]) == 0.0
+    b = api.BatchedInputs([A, A[:20, :20].contiguous()])
+    b.n_max = 30
+    s, l = api.logdet_batched(b, "f32_plain")
+    assert math.isnan(float(s[0])) and math.isnan(float(l[0]))
+    s2, l2 = api.logdet(A[:20, :20].contiguous(), "f32_plain")
+    assert float(s[1]) == float(s2) and float(l[1]) == float(l2)
