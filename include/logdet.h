@@ -123,8 +123,10 @@ ld_status ld_logdet_backward(const void* factors, const double* g, void* grad, i
  *   n_max    host bound on every n[i] (sizes the workspace); n[i] > n_max gives
  *            NaN for that matrix
  *   signs, logabs  device arrays of `count` doubles
- * Modes: LD_F32_PLAIN and LD_F64_PLAIN (one persistent launch, any mix of
- * sizes), and LD_F32_TF32 / LD_F32_3XTF32 / LD_F32_BF16X3 for a batch of one size
+ * Modes: LD_F32_PLAIN and LD_F64_PLAIN (one persistent sweep launch, any mix of
+ * sizes, n_max <= 2760 for FP32 and <= 1296 for FP64, else LD_ERR_UNSUPPORTED;
+ * FP32 adds one launch for the pivots' logs and one for the ordered sums), and
+ * LD_F32_TF32 / LD_F32_3XTF32 / LD_F32_BF16X3 for a batch of one size
  * n_max (n[i] = n_max for every i; another size gives NaN for that matrix): the
  * blocked sweep of ld_logdet run panel by panel across the whole batch (a
  * one-CTA panel kernel per matrix, then batched multipliers and one batched
