@@ -27,3 +27,34 @@ def test_reference_arm_line():
     assert "condensation steps" in cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_roofline_arithmetic():
+    """achieved = algorithmic work / event time; peak from the measured peaks
+    (3xTF32: BF16 sustained x 1.1/2.25 / 3); frac = achieved / peak."""
+    b = _bench_module()
+    peaks = b.read_peaks()
+    # a tensor-bound launch: 1e12 flop and 1e9 bytes in 10 ms over 2 steps
+    r = b.make_roofline("rankb_tc", "f32_3xtf32", 2e9, 2e12, 20.0, 4, 2)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 100.0) < 1e-9
+    want_peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25 / 3.0
+    assert abs(r["peak"] - want_peak) < 1e-9 and abs(r["frac"] - 100.0 / want_peak) < 1e-12
+    assert r["kernel_ms_per_step"] == 10.0 and r["kernel_launches_per_step"] == 2
+    # any other kernel is reported against HBM: 6.6e9 bytes in 1 s
+    r = b.make_roofline("panel", "f32_3xtf32", 6.6e9, 0.0, 1000.0, 1, 1)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 6.6) < 1e-9 and r["peak"] == peaks["hbm_gbs"]
+    # BF16x3 and plain TF32 peaks
+    assert abs(b.make_roofline("rankb_tc", "f32_bf16x3", 1, 1, 1, 1, 1)["peak"]
+               - peaks["bf16_tflops_sustained"] / 3.0) < 1e-9
+    assert abs(b.make_roofline("rankb_tc", "f32_tf32", 1, 1, 1, 1, 1)["peak"]
+               - peaks["bf16_tflops_sustained"] * 1.1 / 2.25) < 1e-9
