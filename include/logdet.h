@@ -57,7 +57,7 @@ typedef enum { LD_DTYPE_F64 = 0, LD_DTYPE_F32 = 1 } ld_dtype;
 typedef enum {
   LD_OK = 0,
   LD_ERR_INVALID_ARG = 1, /* bad size, leading dimension, pointer or enum */
-  LD_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve */
+  LD_ERR_UNSUPPORTED = 2, /* valid request the library cannot serve */
   LD_ERR_ALLOC = 3,       /* device memory allocation failed */
   LD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
   LD_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */

@@ -150,7 +150,7 @@ const char* ld_status_string(ld_status s) {
     case LD_ERR_INVALID_ARG:
       return "LD_ERR_INVALID_ARG: bad size, leading dimension, pointer or enum";
     case LD_ERR_UNSUPPORTED:
-      return "LD_ERR_UNSUPPORTED: request not supported by this build";
+      return "LD_ERR_UNSUPPORTED: request not supported by the library";
     case LD_ERR_ALLOC:
       return "LD_ERR_ALLOC: device memory allocation failed";
     case LD_ERR_CUDA:
