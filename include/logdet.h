@@ -46,7 +46,11 @@ typedef enum {
   LD_F64_PLAIN = 0,   /* FP64 storage, one rank-1 update per pivot (Eq. (2)) */
   LD_F64_BLOCKED = 1, /* FP64 storage, panels of b pivots + FP64 rank-b update */
   LD_F32_PLAIN = 2,   /* FP32 storage, one rank-1 update per pivot */
-  LD_F32_TF32 = 3,    /* FP32 storage, panels + TF32 tensor-core rank-b update */
+  LD_F32_TF32 = 3,    /* FP32 storage, panels + TF32 tensor-core rank-b update.
+                         Approximate: with 10 mantissa bits in the update, an
+                         ill-conditioned matrix can come out with the wrong sign
+                         (the N = 8000 iid Gaussian matrix does); no sign or
+                         accuracy guarantee */
   LD_F32_3XTF32 = 4,  /* FP32 storage, panels + split-TF32 (hi*hi+hi*lo+lo*hi) */
   LD_F32_BF16X3 = 5   /* FP32 storage, panels + split-BF16 (hi*hi+hi*lo+lo*hi) */
 } ld_mode;

@@ -39,7 +39,11 @@ def _check_matrix(A: torch.Tensor):
 
 
 def logdet(A: torch.Tensor, mode="f64_plain", stream=None):
-    """(sign, log|det A|) as 0-d FP64 CUDA tensors (no host synchronisation)."""
+    """(sign, log|det A|) as 0-d FP64 CUDA tensors (no host synchronisation).
+
+    mode "f32_tf32" is approximate: its trailing update keeps 10 mantissa bits,
+    and on an ill-conditioned matrix even the sign can come out wrong.
+    """
     _check_matrix(A)
     n = A.shape[0]
     lda = max(A.stride(0), 1) if n > 0 else 1

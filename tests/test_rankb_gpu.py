@@ -69,3 +69,36 @@ def test_rankb_rejects_bad_k():
                                 None) == 2
     assert _lib.ld_rankb_update(0, 8, 8, 64, A.data_ptr(), 64, A.data_ptr(), 64, A.data_ptr(), 64,
                                 None) == 1
+
+
+def test_bf16x3_error_is_the_split():
+    """Where BF16x3's error comes from. Inputs already representable in BF16 split
+    exactly (lo = 0), so only the tensor cores' FP32 accumulation is left: the
+    error, relative to |A| |B|^T, is at the FP32 level. General FP32 inputs lose
+    the bits past the two 8-bit pieces (up to 2^-16 per product): an error more
+    than ten times larger, at the size that split predicts (about
+    0.3 * 2^-16 * sqrt(3) per product, 1 / sqrt(K) after the sum of K products
+    of random sign)."""
+    M = N = 1024
+    K = 128
+    g = torch.Generator().manual_seed(77)
+    A = torch.randn(M, K, generator=g)
+    B = torch.randn(N, K, generator=g)
+
+    def rms_err(A, B):
+        D = torch.zeros(M, N, device="cuda")
+        Ad, Bd = A.cuda(), B.cuda()
+        assert _lib.ld_rankb_update(5, M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K,
+                                    D.data_ptr(), N, torch.cuda.current_stream().cuda_stream) == 0
+        want = -(A.double() @ B.double().T)
+        scale = A.double().abs() @ B.double().abs().T
+        return ((D.double().cpu() - want) / scale).pow(2).mean().sqrt().item()
+
+    exact = rms_err(A.bfloat16().float(), B.bfloat16().float())
+    general = rms_err(A, B)
+    predicted = 0.3 * 2.0 ** -16 * 3 ** 0.5 / K ** 0.5
+    print(f"BF16x3 rms error: split-exact inputs {exact:.2e}, general {general:.2e} "
+          f"(split estimate {predicted:.2e})")
+    assert exact <= 5e-8
+    assert general >= 10 * exact
+    assert 0.3 * predicted <= general <= 3 * predicted

@@ -55,3 +55,44 @@ def test_noalloc_host_outputs_and_limit():
     # above the fixed workspace's bound: rejected before any device work
     assert _lib.ld_logdet_noalloc(A.data_ptr(), _lib.LD_DTYPE_F64, 1025, 1025, None,
                                   ctypes.addressof(hs), ctypes.addressof(hl)) == 2
+
+
+def test_noalloc_allocates_nothing(monkeypatch):
+    """The entry point's promise: with the library's allocator made to fail
+    (LD_FAULT_INJECT_ALLOC=1, read by the library at each allocation),
+    ld_logdet reports LD_ERR_ALLOC while ld_logdet_noalloc still returns LD_OK and
+    the same result as before."""
+    n = 300
+    A = torch.from_numpy(workloads.dense_gaussian(n, seed=31)).cuda()
+    ref, _ = _both(A)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    monkeypatch.setenv("LD_FAULT_INJECT_ALLOC", "1")
+    try:
+        assert _lib.ld_logdet(A.data_ptr(), _lib.LD_DTYPE_F64, n, n, _lib.LD_F64_PLAIN, stream,
+                              out.data_ptr(), out.data_ptr() + 8) == 3
+        assert _lib.ld_logdet_noalloc(A.data_ptr(), _lib.LD_DTYPE_F64, n, n, stream,
+                                      out.data_ptr(), out.data_ptr() + 8) == 0
+    finally:
+        monkeypatch.delenv("LD_FAULT_INJECT_ALLOC")
+    got = out.cpu().numpy()
+    assert got[0] == ref[0] and abs(got[1] - ref[1]) <= TOL * max(1.0, abs(ref[1]))
+
+
+def test_noalloc_fp32_input():
+    """FP32 input is widened into the FP64 sweep, exactly as ld_logdet does for
+    FP32 input in the FP64 plain mode."""
+    n = 500
+    A = torch.from_numpy(workloads.dense_gaussian(n, seed=12)).float().cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    ref = torch.empty(2, dtype=torch.float64, device="cuda")
+    got = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    assert _lib.ld_logdet(A.data_ptr(), _lib.LD_DTYPE_F32, n, n, _lib.LD_F64_PLAIN, stream,
+                          ref.data_ptr(), ref.data_ptr() + 8) == 0
+    for _ in range(2):
+        assert _lib.ld_logdet_noalloc(A.data_ptr(), _lib.LD_DTYPE_F32, n, n, stream,
+                                      got.data_ptr(), got.data_ptr() + 8) == 0
+        torch.cuda.synchronize()
+        r, g = ref.cpu().numpy(), got.cpu().numpy()
+        assert g[0] == r[0]
+        assert abs(g[1] - r[1]) <= TOL * max(1.0, abs(r[1]))
