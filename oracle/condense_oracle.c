@@ -30,6 +30,14 @@
  * with -ffp-contract=off so that no other expression is contracted. The sum of
  * log|a_kl| is compensated (Neumaier's variant of Kahan summation).
  *
+ * Other choices the paper names (oracle_logdet_ex):
+ *  - Sec. 1: earlier work picks the pivot column differently: the smallest column
+ *    index with a nonzero entry (rule 2), or the nonzero entry whose value is
+ *    closest to 1 (rule 1; closeness is measured on |a_kj|, as in the Sec. 2.2
+ *    example of entries 1e-10 and 2.01); ties go to the first such column.
+ *  - Sec. 1 and Sec. 2.3: a_kl may be factored out of column l instead of row k:
+ *    c_i = a_il / a_kl and each minor is fma(-c_i, a_kj, a_ij).
+ *
  * Conventions where the paper is silent: n == 0 gives (sign 1, logabs 0); a
  * pivot row that is all zero gives (0, -inf) and stops; a NaN anywhere in a
  * pivot row gives (NaN, NaN) and stops.
@@ -77,6 +85,27 @@ static int64_t pivot_column(const double *W, int64_t m) {
   return l;
 }
 
+/* Pivot column of row 0 under the rules of earlier work (Sec. 1): rule 1 the
+ * first nonzero entry closest to 1 in absolute value (smallest | |w| - 1 |),
+ * rule 2 the first nonzero entry. Column 0 when the row is all zero (the caller
+ * then sees a zero pivot); -1 when the row holds a NaN. */
+static int64_t pivot_column_rule(const double *W, int64_t m, int rule) {
+  int64_t l = -1;
+  double best = 0.0;
+  for (int64_t j = 0; j < m; ++j)
+    if (isnan(W[j])) return -1;
+  for (int64_t j = 0; j < m; ++j) {
+    if (W[j] == 0.0) continue;
+    if (rule == 2) return j;
+    const double d = fabs(fabs(W[j]) - 1.0);
+    if (l < 0 || d < best) {
+      best = d;
+      l = j;
+    }
+  }
+  return l < 0 ? 0 : l;
+}
+
 /* Eq. (2) with the row-factored pivot of Eq. (3): rows i0..i1-1 (i >= 1) of the
  * new matrix. W is m x m (leading dimension m), r is the factored pivot row,
  * Wn is (m-1) x (m-1). Row 0 (the pivot row k) and column l are dropped,
@@ -95,13 +124,39 @@ static void condense_rows(const double *W, int64_t m, int64_t l, const double *r
   }
 }
 
+/* Eq. (2) with the pivot factored out of COLUMN l instead (Sec. 2.3): the
+ * multiplier c_i = a_il / a_kl, and each minor is fma(-c_i, a_kj, a_ij); row 0
+ * of W is the unfactored pivot row. */
+static void condense_rows_colf(const double *W, int64_t m, int64_t l, double p, double *Wn,
+                               int64_t i0, int64_t i1) {
+  for (int64_t i = i0; i < i1; ++i) {
+    const double *wi = W + i * m;
+    double *out = Wn + (i - 1) * (m - 1);
+    const double c_i = wi[l] / p;
+    int64_t jj = 0;
+    for (int64_t j = 0; j < m; ++j) {
+      if (j == l) continue;
+      out[jj++] = fma(-c_i, W[j], wi[j]);
+    }
+  }
+}
+
 /* ---- a small fixed thread team for the row loop ---- */
 typedef struct {
   const double *W;
   double *Wn;
   const double *r;
   int64_t m, l;
+  double p;
+  int colf; /* 1: column-factored minors (condense_rows_colf) */
 } job_t;
+
+static void job_rows(const job_t *job, int64_t i0, int64_t i1) {
+  if (job->colf)
+    condense_rows_colf(job->W, job->m, job->l, job->p, job->Wn, i0, i1);
+  else
+    condense_rows(job->W, job->m, job->l, job->r, job->Wn, i0, i1);
+}
 
 typedef struct team team_t;
 typedef struct {
@@ -135,7 +190,7 @@ static void *team_worker(void *p) {
     if (t->quit) break;
     int64_t i0, i1;
     team_rows(&t->job, wa->id, t->nthreads, &i0, &i1);
-    condense_rows(t->job.W, t->job.m, t->job.l, t->job.r, t->job.Wn, i0, i1);
+    job_rows(&t->job, i0, i1);
     pthread_barrier_wait(&t->done);
   }
   return NULL;
@@ -160,14 +215,14 @@ static int team_start(team_t *t, int nthreads) {
 
 static void team_run(team_t *t, const job_t *job) {
   if (t->nthreads <= 1) {
-    condense_rows(job->W, job->m, job->l, job->r, job->Wn, 1, job->m);
+    job_rows(job, 1, job->m);
     return;
   }
   t->job = *job;
   pthread_barrier_wait(&t->start);
   int64_t i0, i1;
   team_rows(job, 0, t->nthreads, &i0, &i1);
-  condense_rows(job->W, job->m, job->l, job->r, job->Wn, i0, i1);
+  job_rows(job, i0, i1);
   pthread_barrier_wait(&t->done);
 }
 
@@ -190,6 +245,9 @@ static void team_stop(team_t *t) {
  *   max_steps  < 0: run to the end. >= 0: stop after that many condensation
  *              steps (a bounded sample for timing; sign/logabs are then partial)
  *   nthreads   threads for the row loop (>= 1)
+ *   rule       pivot column: 0 max |a_kj| (Sec. 2.2, the paper's), 1 the nonzero
+ *              |a_kj| closest to 1, 2 the first nonzero (earlier work, Sec. 1)
+ *   colf       0: a_kl factored out of row k; 1: out of column l (Sec. 2.3)
  *   sign       out: +1, -1, 0 (singular) or NaN
  *   logabs     out: log|det A|, -inf when singular, NaN on NaN input
  *   piv_label  out (may be NULL): n entries, original column label of the pivot
@@ -198,10 +256,11 @@ static void team_stop(team_t *t) {
  *   steps_done out (may be NULL): number of pivots taken
  * Returns 0, or 1 for bad arguments, 2 when host memory runs out.
  */
-int oracle_logdet(const double *A, int64_t n, int64_t lda, int64_t max_steps, int nthreads,
-                  double *sign, double *logabs, int64_t *piv_label, double *piv_value,
-                  int64_t *steps_done) {
+int oracle_logdet_ex(const double *A, int64_t n, int64_t lda, int64_t max_steps, int nthreads,
+                     int rule, int colf, double *sign, double *logabs, int64_t *piv_label,
+                     double *piv_value, int64_t *steps_done) {
   if (n < 0 || lda < n || (n > 0 && !A) || !sign || !logabs || nthreads < 1) return ORACLE_BAD_ARG;
+  if (rule < 0 || rule > 2 || colf < 0 || colf > 1) return ORACLE_BAD_ARG;
   for (int64_t s = 0; s < n; ++s) {
     if (piv_label) piv_label[s] = -1;
     if (piv_value) piv_value[s] = 0.0;
@@ -234,7 +293,7 @@ int oracle_logdet(const double *A, int64_t n, int64_t lda, int64_t max_steps, in
   int done = 0;
   while (!done) {
     if (max_steps >= 0 && step >= max_steps) break;
-    int64_t l = pivot_column(W, m);
+    int64_t l = rule == 0 ? pivot_column(W, m) : pivot_column_rule(W, m, rule);
     if (l < 0) { /* NaN in the pivot row */
       sgn = NAN;
       acc.s = NAN;
@@ -260,8 +319,9 @@ int oracle_logdet(const double *A, int64_t n, int64_t lda, int64_t max_steps, in
       done = 1;
       break;
     }
-    for (int64_t j = 0; j < m; ++j) r[j] = W[j] / p; /* pivot row factored (Sec. 2.3) */
-    job_t job = {W, Wn, r, m, l};
+    if (!colf)
+      for (int64_t j = 0; j < m; ++j) r[j] = W[j] / p; /* pivot row factored (Sec. 2.3) */
+    job_t job = {W, Wn, r, m, l, p, colf};
     team_run(&team, &job);
     for (int64_t j = l; j + 1 < m; ++j) label[j] = label[j + 1]; /* drop column l */
     double *tmp = W;
@@ -275,6 +335,14 @@ int oracle_logdet(const double *A, int64_t n, int64_t lda, int64_t max_steps, in
   if (steps_done) *steps_done = step;
   free(W); free(Wn); free(r); free(label);
   return ORACLE_OK;
+}
+
+/* The paper's method: max-abs pivot column, pivot factored out of the row. */
+int oracle_logdet(const double *A, int64_t n, int64_t lda, int64_t max_steps, int nthreads,
+                  double *sign, double *logabs, int64_t *piv_label, double *piv_value,
+                  int64_t *steps_done) {
+  return oracle_logdet_ex(A, n, lda, max_steps, nthreads, 0, 0, sign, logabs, piv_label,
+                          piv_value, steps_done);
 }
 
 /*

@@ -54,6 +54,9 @@ def _bind(path: str):
     pi = ctypes.POINTER(i64)
     lib.oracle_logdet.argtypes = [pd, i64, i64, i64, ctypes.c_int, pd, pd, pi, pd, pi]
     lib.oracle_logdet.restype = ctypes.c_int
+    lib.oracle_logdet_ex.argtypes = [pd, i64, i64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     pd, pd, pi, pd, pi]
+    lib.oracle_logdet_ex.restype = ctypes.c_int
     lib.oracle_condense_once.argtypes = [pd, i64, i64, i64, i64, pd, pd]
     lib.oracle_condense_once.restype = ctypes.c_int
     return lib
@@ -86,8 +89,19 @@ def _as_f64(A) -> np.ndarray:
     return np.ascontiguousarray(A)
 
 
-def logdet(A, *, max_steps: int = -1, nthreads: int = 1, _library: str | None = None) -> OracleResult:
-    """sign(det A), log|det A| and the pivot sequence, FP64 (Eqs. (2)-(3), Sec. 2.2)."""
+# pivot-column rules (oracle_logdet_ex): the paper's max |a_kj| (Sec. 2.2) and the
+# two rules of earlier work it names (Sec. 1)
+RULES = {"max_abs": 0, "closest_to_one": 1, "first_nonzero": 2}
+
+
+def logdet(A, *, max_steps: int = -1, nthreads: int = 1, rule: str = "max_abs",
+           factor: str = "row", _library: str | None = None) -> OracleResult:
+    """sign(det A), log|det A| and the pivot sequence, FP64 (Eqs. (2)-(3), Sec. 2.2).
+
+    rule: pivot column "max_abs" (the paper's), "closest_to_one" or
+    "first_nonzero" (Sec. 1); factor: the pivot factored out of the "row" (the
+    paper's) or the "column" (Sec. 2.3).
+    """
     lib = _load(_library)
     A = _as_f64(A)
     n = A.shape[0]
@@ -98,9 +112,18 @@ def logdet(A, *, max_steps: int = -1, nthreads: int = 1, _library: str | None = 
     val = np.empty(max(n, 1), dtype=np.float64)
     pd = ctypes.POINTER(ctypes.c_double)
     pi = ctypes.POINTER(ctypes.c_int64)
-    rc = lib.oracle_logdet(A.ctypes.data_as(pd), n, n, max_steps, int(nthreads),
-                           ctypes.byref(sign), ctypes.byref(logabs),
-                           lab.ctypes.data_as(pi), val.ctypes.data_as(pd), ctypes.byref(steps))
+    if factor not in ("row", "column"):
+        raise ValueError("factor must be 'row' or 'column'")
+    if rule == "max_abs" and factor == "row":
+        rc = lib.oracle_logdet(A.ctypes.data_as(pd), n, n, max_steps, int(nthreads),
+                               ctypes.byref(sign), ctypes.byref(logabs),
+                               lab.ctypes.data_as(pi), val.ctypes.data_as(pd), ctypes.byref(steps))
+    else:
+        rc = lib.oracle_logdet_ex(A.ctypes.data_as(pd), n, n, max_steps, int(nthreads),
+                                  RULES[rule], 1 if factor == "column" else 0,
+                                  ctypes.byref(sign), ctypes.byref(logabs),
+                                  lab.ctypes.data_as(pi), val.ctypes.data_as(pd),
+                                  ctypes.byref(steps))
     if rc != 0:
         raise RuntimeError(f"oracle_logdet failed with code {rc}")
     return OracleResult(sign.value, logabs.value, lab[:n].copy(), val[:n].copy(), steps.value)
