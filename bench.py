@@ -1,11 +1,17 @@
 """Benchmark: condensation log-determinant throughput on GB300 (one JSON line).
 
 A step is one full condensation sweep (stage, every pivot step, finalize) of the
-N x N benchmark matrix through liblogdet. Throughput is counted as 2N^3/3 flop
-per sweep (TFLOP/s). Inputs: dense iid N(0, 1/N) entries, N = 8000, seed 1,
-generated with numpy's default_rng (bit-identical on every host).
+N x N benchmark matrix through liblogdet; throughput is counted as 2N^3/3 flop
+per sweep (TFLOP/s). The default line is the largest single-GPU workload:
+N = 32768, A = Q diag(lambda) Q^T with Q Haar (QR of a Gaussian) and lambda
+log-uniform in [1e-4, 1] (seed 2), stored in FP32, swept with the trailing update
+in split TF32 (3xTF32); its error is taken against the exact sum of log(lambda).
+Every other workload (N = 16384 of the same recipe, the N = 8000 iid and
+covariance matrices in every mode, the 4096-matrix batch and the 256-matrix
+gradient) is measured beside it under "paths", each with its error and roofline.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f64_plain]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f32_3xtf32]
+                    [--workload spd32768|spd16384|dense|spdcov8000|batched4096|grad256x1024]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 With N > 1 (torchrun), every rank runs an independent replica of the sweep (a
@@ -27,13 +33,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "logdet TFLOP/s (2N³/3) and batched dets/s, mixed vs plain FP64 at stated error"
 UNIT = "TFLOP/s"
-N_DEFAULT = 8000
-SEED = 1
 
 # nominal dense tensor rates relative to BF16 (TF32 1.1 / BF16 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 DTYPE = {"f64_plain": "f64", "f32_plain": "f32", "f64_blocked": "f64", "f32_tf32": "f32+tf32",
          "f32_3xtf32": "f32+3xtf32", "f32_bf16x3": "f32+bf16x3"}
+TENSOR_MODES = ("f32_tf32", "f32_3xtf32", "f32_bf16x3")
+ALL_MODES = ["f64_plain", "f32_plain", "f64_blocked", "f32_tf32", "f32_3xtf32", "f32_bf16x3"]
+
+# single-matrix workloads: (N, description)
+WORKLOADS = {
+    "spd32768": (32768, "SPD Q diag(lambda) Q^T, Q Haar, lambda log-uniform [1e-4,1], seed 2, "
+                        "N=32768, FP32 storage; error vs exact sum log(lambda)"),
+    "spd16384": (16384, "SPD Q diag(lambda) Q^T, Q Haar, lambda log-uniform [1e-4,1], seed 2, "
+                        "N=16384, FP32 storage; error vs exact sum log(lambda)"),
+    "dense": (8000, "dense iid N(0,1/N), seed 1; error vs the stored FP64 oracle result"),
+    "spdcov8000": (8000, "SPD X^T X/(2N)+1e-3 I, X 2N x N iid N(0,1) drawn after the dense "
+                         "matrix of seed 1, N=8000; error vs the stored FP64 oracle result"),
+}
 
 
 def flops(N):
@@ -49,6 +66,19 @@ def read_peaks():
                 "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "source": "fallback"}
+
+
+def tensor_peak(mode, peaks=None):
+    """Dense tensor peak of the trailing update's arithmetic, in useful (FP32-
+    equivalent) TFLOP/s: the measured sustained BF16 rate, times the nominal
+    TF32/BF16 ratio for TF32, divided by the three products of the split kinds."""
+    peaks = peaks or read_peaks()
+    bf16 = peaks["bf16_tflops_sustained"]
+    if mode == "f32_bf16x3":
+        return bf16 / 3.0, "BF16 sustained / 3 (three products)"
+    if mode == "f32_3xtf32":
+        return bf16 * TF32_OVER_BF16 / 3.0, "BF16 sustained x 1.1/2.25 (TF32) / 3"
+    return bf16 * TF32_OVER_BF16, "BF16 sustained x 1.1/2.25 (TF32)"
 
 
 def env_rank():
@@ -104,15 +134,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ inputs
+def make_input(workload, N, dev):
+    """(A on dev, reference logabs, reference sign, reference note). The SPD
+    recipes are generated on the GPU in FP64 and stored in FP32; the iid and
+    covariance matrices on the host in FP64 (numpy default_rng)."""
+    import torch
+    import workloads
+    if workload in ("spd32768", "spd16384"):
+        A, sl = workloads.spd_haar_torch(N, seed=2, lo=1e-4, hi=1.0, device=dev,
+                                         dtype=torch.float32)
+        return A, sl, 1.0, "exact sum of log(lambda)"
+    if workload == "dense":
+        A = torch.from_numpy(workloads.dense_gaussian(N, seed=1, var=1.0 / N)).to(dev)
+        gold = os.path.join(ROOT, "tests", "golden", f"oracle_dense_n{N}_seed1.json")
+    else:
+        A = torch.from_numpy(workloads.dense_and_spd_pair(N, seed=1)[1]).to(dev)
+        gold = os.path.join(ROOT, "tests", "golden", f"oracle_spd_n{N}_seed1.json")
+    if os.path.exists(gold):
+        with open(gold) as f:
+            g = json.load(f)
+        return A, g["logabs"], g["sign"], "stored FP64 oracle result"
+    return A, None, None, None
+
+
+def accuracy(sg, la, ref, ref_sign):
+    if ref is None:
+        return None
+    return {"logabs": float(la), "ref_logabs": ref,
+            "rel_err": abs(float(la) - ref) / max(1.0, abs(ref)),
+            "sign_match": float(sg) == ref_sign}
+
+
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(A, target_s=12.0, threads=None):
-    """Times the oracle on the host cores over the first S pivot steps of A."""
+def oracle_sample(A, target_s=12.0, threads=None, what="benchmark matrix"):
+    """Times the oracle on the host cores over the first S pivot steps of A
+    (S sized for about target_s seconds)."""
     import oracle
 
     N = A.shape[0]
     threads = threads or (os.cpu_count() or 1)
     oracle.build()
-    s0 = min(N, 8)
+    s0 = min(N, 4)
     t0 = time.perf_counter()
     oracle.logdet(A, max_steps=s0, nthreads=threads)
     t_cal = max(time.perf_counter() - t0, 1e-3)
@@ -121,24 +184,55 @@ def oracle_sample(A, target_s=12.0, threads=None):
     oracle.logdet(A, max_steps=S, nthreads=threads)
     dt = time.perf_counter() - t0
     fl = sum(2.0 * (N - s - 1) ** 2 for s in range(S))
+    share = fl / flops(N)
     return {"value": fl / dt / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {S} of {N} condensation steps of the N={N} benchmark matrix "
-                      f"({fl:.3g} flop in {dt:.2f} s, FP64, {threads} threads)"}
+            "sample": f"first {S} of {N} condensation steps of the N={N} {what} ({fl:.3g} flop, "
+                      f"{100 * share:.1f}% of the sweep's, in {dt:.2f} s, FP64, {threads} threads)"}
+
+
+def oracle_full_sweep(A, threads=None, what="matrix"):
+    """Times one whole oracle sweep of A on the host cores."""
+    import oracle
+
+    N = A.shape[0]
+    threads = threads or (os.cpu_count() or 1)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.logdet(A, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": flops(N) / dt / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "seconds": dt, "sample": f"the whole sweep of the N={N} {what} (FP64, {threads} threads)"}
+
+
+def host_matrix(workload, N):
+    """The workload's matrix on the host in FP64 (for the oracle)."""
+    import numpy as np
+    import workloads
+    if workload == "dense":
+        return workloads.dense_gaussian(N, seed=1, var=1.0 / N)
+    if workload == "spdcov8000":
+        return workloads.dense_and_spd_pair(N, seed=1)[1]
+    import torch
+    A, _ = workloads.spd_haar_torch(N, seed=2, lo=1e-4, hi=1.0, device="cuda",
+                                    dtype=torch.float32)
+    out = A.cpu().double().numpy()
+    del A
+    torch.cuda.empty_cache()
+    return np.ascontiguousarray(out)
 
 
 def run_reference(args):
+    """The oracle on the host cores, on bounded samples of this benchmark's workload."""
     rank, _, world = env_rank()
     if rank != 0:
         return 0
-    import workloads
-    N = args.N
-    A = workloads.dense_gaussian(N, seed=SEED, var=1.0 / N)
+    N = args.N or WORKLOADS[args.workload][0]
+    A = host_matrix(args.workload, N)
     # each step: a bounded sample of the sweep, sized so the whole run takes minutes
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(A, target_s=per_step * 0.3)
-    vals = []
-    samples = []
+    vals, samples = [], []
     for _ in range(args.steps):
         cb = oracle_sample(A, target_s=per_step)
         vals.append(cb["value"])
@@ -151,8 +245,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": flops(N) / (v * 1e12) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"dense iid N(0,1/N) N={N} seed {SEED}, plain FP64 condensation "
-                               f"(oracle, host cores)", "N": N, "mode": "f64_plain"},
+        "config": {"workload": WORKLOADS[args.workload][1] +
+                   ", plain FP64 condensation (oracle, host cores)", "N": N, "mode": "f64_plain"},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -161,14 +255,10 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ rooflines
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# dominant kernel, from one ncu capture of the kernel as it stands; keyed by
-# (kernel class, workload). Reported only for the workload it was taken on.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel, from one ncu capture of the kernel as it stands; keyed by (kernel
+# class, workload). Reported only for the workload it was taken on.
 NCU_TRAFFIC = {
-    ("panel", "dense N=8000 f32_3xtf32"): {
-        "bytes": 3868928 + 256,
-        "launch": "6th panel of a sweep (m0 = 7360); its declared algorithmic bytes: 67.8e6",
-        "summary": "profiles/panel_cluster_kernel_n8000.md"},
     ("batched", "batched4096"): {
         "bytes": 11386784000 + 11559038000,
         "launch": "the whole batch (one launch per step)",
@@ -177,6 +267,9 @@ NCU_TRAFFIC = {
 
 
 def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
+    """Roofline of one kernel class: its algorithmic work over its summed event
+    time. The tensor-core update is tensor-bound; the others are reported against
+    HBM."""
     peaks = read_peaks()
     sec = k_ms * 1e-3
     out = {"kernel": kernel, "traffic": None, "peak_source": peaks["source"],
@@ -184,24 +277,75 @@ def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
            "algorithmic_bytes_per_step": k_bytes / steps,
            "algorithmic_flops_per_step": k_flops / steps}
     if kernel == "rankb_tc":
-        # tensor-bound contraction; split modes run 3 products per useful flop
-        bf16 = peaks["bf16_tflops_sustained"]
-        if mode == "f32_bf16x3":
-            peak, note = bf16 / 3.0, "BF16 sustained / 3 (three products)"
-        elif mode == "f32_3xtf32":
-            peak, note = bf16 * TF32_OVER_BF16 / 3.0, "BF16 sustained x 1.1/2.25 (TF32) / 3"
-        else:
-            peak, note = bf16 * TF32_OVER_BF16, "BF16 sustained x 1.1/2.25 (TF32)"
+        peak, note = tensor_peak(mode, peaks)
         ach = k_flops / sec / 1e12 if sec > 0 else None
         out.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak if ach else None, "peak_note": note})
-        hbm = k_bytes / sec / 1e9 if sec > 0 else None
-        out["hbm_gbs_same_kernel"] = hbm
+        out["hbm_gbs_same_kernel"] = k_bytes / sec / 1e9 if sec > 0 else None
     else:
         ach = k_bytes / sec / 1e9 if sec > 0 else None
         peak = peaks["hbm_gbs"]
         out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak if ach else None})
+    return out
+
+
+def profile_step(_lib, step, dev):
+    """One step with every launch accounted: per-class launches, event time and
+    declared work."""
+    import torch
+    _lib.ld_profile_start(None)
+    step()
+    torch.cuda.synchronize(dev)
+    _lib.ld_profile_stop()
+    shares = {}
+    for cls in _lib.ld_profile_classes():
+        nl, tms = _lib.ld_profile_query(cls)
+        b, f = _lib.ld_profile_work(cls)
+        shares[cls] = {"launches": nl, "ms": round(tms, 4), "bytes": b, "flops": f}
+    tot = sum(v["ms"] for v in shares.values()) or 1.0
+    for v in shares.values():
+        v["share"] = round(v["ms"] / tot, 4)
+    return shares
+
+
+def sweep_roofline(mode, N, ms, shares):
+    """The sweep-level figure: 2N^3/3 useful flop per sweep over the sweep's time,
+    against the tensor peak of the update's arithmetic (tensor-core modes), plus
+    the tensor-core update's own roofline and the panel chain's time per pivot.
+    Plain modes: the rank-1 update kernel against HBM."""
+    peaks = read_peaks()
+    out = {}
+    if mode in TENSOR_MODES:
+        peak, note = tensor_peak(mode, peaks)
+        ach = flops(N) / (ms * 1e-3) / 1e12
+        out = {"kernel": "whole sweep (all kernels, one step)", "bound": "tensor",
+               "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_note": note + " (measured sustained BF16; peak_source " + peaks["source"] + ")",
+               "traffic": None,
+               "traffic_note": "a whole sweep is many launches; the DRAM bytes per launch of its "
+                               "dominant kernel are under tensor_update"}
+        if "rankb_tc" in shares:
+            s = shares["rankb_tc"]
+            out["tensor_update"] = make_roofline("rankb_tc", mode, s["bytes"], s["flops"], s["ms"],
+                                                 s["launches"], 1)
+    elif mode == "f64_blocked":
+        ach = flops(N) / (ms * 1e-3) / 1e12
+        out = {"kernel": "whole sweep (all kernels, one step)", "bound": "fp64",
+               "achieved": ach, "unit": "TFLOP/s", "peak": None, "frac": None,
+               "peak_note": "the FP64 FMA rate of this GPU is not in the measured peaks"}
+    if "panel" in shares:
+        out["pivot_chain"] = {"pivots_per_step": N, "panel_ms": shares["panel"]["ms"],
+                              "us_per_pivot": 1e3 * shares["panel"]["ms"] / N}
+    if "update" in shares:
+        s = shares["update"]
+        upd = make_roofline("update", mode, s["bytes"], s["flops"], s["ms"], s["launches"], 1)
+        if not out:
+            out = upd
+        else:
+            out["rank1_update"] = upd
+    out["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
+                            for k, v in shares.items()}
     return out
 
 
@@ -220,63 +364,59 @@ def time_call(fn, warmup, steps, dev):
     return e0.elapsed_time(e1) / steps, r
 
 
-def other_paths(pk, _lib, A, main_mode, dev, err_gold=None):
-    """Quick timings of the other paths (each entry independent; errors recorded)."""
+def measure_path(pk, _lib, A, mode, ref, ref_sign, dev, steps=2):
+    """Time, error and roofline of one sweep mode on one matrix."""
+    N = A.shape[0]
+    ms, (sg, la) = time_call(lambda: pk.logdet(A, mode), 1, steps, dev)
+    shares = profile_step(_lib, lambda: pk.logdet(A, mode), dev)
+    e = {"ms_per_sweep": ms, "tflops": flops(N) / (ms * 1e-3) / 1e12,
+         "roofline": sweep_roofline(mode, N, ms, shares)}
+    acc = accuracy(sg, la, ref, ref_sign)
+    if acc:
+        e["rel_err"] = acc["rel_err"]
+        e["sign_match"] = acc["sign_match"]
+    return e
+
+
+def other_paths(pk, _lib, dev, main_workload, main_mode, A_main, ref_main):
+    """Every other config of the benchmark, each entry independent (errors are
+    recorded, not raised)."""
     import torch
     import workloads
     res = {}
-    N = A.shape[0]
-    g = None
-    if err_gold and os.path.exists(err_gold):
-        with open(err_gold) as f:
-            g = json.load(f)
-    for mode in ["f64_plain", "f32_plain", "f64_blocked", "f32_tf32", "f32_3xtf32", "f32_bf16x3"]:
+    # the headline matrix in its other tensor-core modes
+    for mode in TENSOR_MODES:
         if mode == main_mode:
             continue
         try:
-            steps = 1 if mode in ("f64_plain", "f32_plain", "f64_blocked") else 3
-            ms, (sg, la) = time_call(lambda: pk.logdet(A, mode), 1, steps, dev)
-            e = {"ms_per_sweep": ms, "tflops": flops(N) / (ms * 1e-3) / 1e12}
-            if g:
-                e["rel_err_vs_oracle"] = abs(float(la) - g["logabs"]) / max(1.0, abs(g["logabs"]))
-                e["sign_match"] = float(sg) == g["sign"]
-            res[mode] = e
-        except Exception as ex:  # report, do not fail the benchmark line
-            res[mode] = {"error": str(ex)[:200]}
-    try:
-        sizes = workloads.batched_sizes(4096, seed=3)
-        mats = workloads.batched_covariances_torch(sizes, seed=3, device=dev)
-        batch = pk.BatchedInputs(mats)
-        ms, _ = time_call(lambda: pk.logdet_batched(batch, "f32_plain"), 2, 5, dev)
-        fl = float(sum(2.0 * int(n) ** 3 / 3.0 for n in sizes))
-        res["batched_4096_f32"] = {"ms": ms, "dets_per_s": 4096 / (ms * 1e-3),
-                                   "tflops": fl / (ms * 1e-3) / 1e12,
-                                   "workload": "4096 SPD X^T X/(2n)+1e-2 I, n uniform on "
-                                               "{32,...,512}, seed 3, FP32, one launch"}
-        del mats, batch
-    except Exception as ex:
-        res["batched_4096_f32"] = {"error": str(ex)[:200]}
-    try:
-        B, n = 256, 1024
-        gen = torch.Generator(device=dev).manual_seed(4)
-        lam = 10.0 ** (-2.0 * torch.rand(B, n, generator=gen, device=dev, dtype=torch.float64))
-        Q, R = torch.linalg.qr(torch.randn(B, n, n, generator=gen, device=dev, dtype=torch.float64))
-        Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
-        X = ((Q * lam[:, None, :]) @ Q.transpose(1, 2)).float()
-        del Q, R
-
-        for gm in ("f32_3xtf32", "f32_plain"):
-            def fb():
-                Xg = X.detach().requires_grad_(True)
-                out = pk.logabsdet(Xg, gm)
-                out.sum().backward()
-                return Xg.grad
-            ms, _ = time_call(fb, 1, 2, dev)
-            res[f"grad_256x1024_{gm}"] = {"ms_forward_backward": ms,
-                                          "fwd_bwd_tflops": (B * (2 * n ** 3 / 3 + 2 * n ** 3)) /
-                                          (ms * 1e-3) / 1e12}
-    except Exception as ex:
-        res["grad_256x1024"] = {"error": str(ex)[:200]}
+            res[f"{main_workload}_{mode}"] = measure_path(pk, _lib, A_main, mode, ref_main, 1.0, dev)
+        except Exception as ex:
+            res[f"{main_workload}_{mode}"] = {"error": str(ex)[:200]}
+    # the other single-matrix configs
+    for wl, modes in (("spd16384", TENSOR_MODES), ("dense", ALL_MODES), ("spdcov8000", ALL_MODES)):
+        if wl == main_workload:
+            continue
+        try:
+            N = WORKLOADS[wl][0]
+            A, ref, ref_sign, note = make_input(wl, N, dev)
+            for mode in modes:
+                try:
+                    steps = 1 if mode in ("f64_plain", "f32_plain", "f64_blocked") else 2
+                    e = measure_path(pk, _lib, A, mode, ref, ref_sign, dev, steps=steps)
+                    e["workload"] = WORKLOADS[wl][1]
+                    res[f"{wl}_{mode}"] = e
+                except Exception as ex:
+                    res[f"{wl}_{mode}"] = {"error": str(ex)[:200]}
+            del A
+            torch.cuda.empty_cache()
+        except Exception as ex:
+            res[wl] = {"error": str(ex)[:200]}
+    # the batch and the gradient workloads (their own lines with --workload)
+    for wl in ("batched4096", "grad256x1024"):
+        try:
+            res[wl] = other_workload_line(wl, pk, _lib, dev, 2, 5)
+        except Exception as ex:
+            res[wl] = {"error": str(ex)[:200]}
     return res
 
 
@@ -293,15 +433,21 @@ def run_ours(args):
 
     import paper_1811_08057_gb300 as pk
     from paper_1811_08057_gb300 import _lib
-    import workloads
 
-    N = args.N
-    mode = args.mode
     stream = torch.cuda.current_stream(dev)
-    if args.workload != "dense":
-        return run_other_workload(args, pk, _lib, dev, stream, rank, world)
-    A_np = workloads.dense_gaussian(N, seed=SEED, var=1.0 / N)
-    A = torch.from_numpy(A_np).to(dev)
+    if args.workload in ("batched4096", "grad256x1024"):
+        line = other_workload_line(args.workload, pk, _lib, dev, args.warmup, args.steps,
+                                   world=world, full=True)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    N = args.N or WORKLOADS[args.workload][0]
+    mode = args.mode
+    A, ref, ref_sign, ref_note = make_input(args.workload, N, dev)
+    torch.cuda.synchronize(dev)
 
     def step():
         return pk.logdet(A, mode)
@@ -314,35 +460,19 @@ def run_ours(args):
     for _ in range(args.warmup):
         sg, la = step()
     barrier()
+    err = accuracy(sg, la, ref, ref_sign)
+    if err:
+        err["reference"] = ref_note
 
-    # accuracy of this result against the stored FP64 oracle value
-    err = None
-    gold = os.path.join(ROOT, "tests", "golden", f"oracle_dense_n{N}_seed{SEED}.json")
-    if os.path.exists(gold):
-        with open(gold) as f:
-            g = json.load(f)
-        err = {"logabs": float(la), "oracle_logabs": g["logabs"],
-               "rel_err": abs(float(la) - g["logabs"]) / max(1.0, abs(g["logabs"])),
-               "sign_match": float(sg) == g["sign"]}
+    # one fully profiled sweep: per-class launches, time and declared work
+    shares = profile_step(_lib, step, dev)
+    dominant = max(shares, key=lambda k: shares[k]["ms"]) if shares else None
 
-    # one fully profiled sweep: per-class shares, then the dominant class
-    _lib.ld_profile_start(None)
-    step()
-    torch.cuda.synchronize(dev)
-    _lib.ld_profile_stop()
-    shares = {}
-    for cls in _lib.ld_profile_classes():
-        nl, tms = _lib.ld_profile_query(cls)
-        shares[cls] = {"launches": nl, "ms": round(tms, 4)}
-    tot = sum(v["ms"] for v in shares.values()) or 1.0
-    for v in shares.values():
-        v["share"] = round(v["ms"] / tot, 4)
-    kernel = max(shares, key=lambda k: shares[k]["ms"]) if shares else "update"
-    # the tensor-core trailing update of the same profiled sweep (its own event time)
-    tc_work = _lib.ld_profile_work("rankb_tc") if "rankb_tc" in shares else None
     clocks = ClockSampler(local)
     time.sleep(0.3)
-    _lib.ld_profile_start(kernel)
+    # inside the timed region only the dominant kernel's launches carry events
+    # (every launch is still counted)
+    _lib.ld_profile_start(dominant)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -355,43 +485,36 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     launches_all, _ = _lib.ld_profile_query(None)
-    k_launches, k_ms = _lib.ld_profile_query(kernel)
-
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t[0])
     value = world * flops(N) / (ms_max * 1e-3) / 1e12
 
-    # roofline of the dominant kernel: algorithmic work over its event time
-    k_bytes, k_flops = _lib.ld_profile_work(kernel)
-    roofline = make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, args.steps)
-    tr = NCU_TRAFFIC.get((kernel, f"dense N={N} {mode}"))
-    if tr:
-        roofline["traffic"] = tr["bytes"]
-        roofline["traffic_note"] = f"ncu, one launch: {tr['launch']} ({tr['summary']})"
-    if kernel == "panel":
-        # the panel is a serial chain of pivots: its time per pivot is the figure to cut
-        roofline["pivot_chain"] = {"pivots_per_step": N,
-                                   "us_per_pivot": 1e3 * k_ms / args.steps / N}
-    if tc_work and kernel != "rankb_tc":
-        roofline["secondary"] = make_roofline("rankb_tc", mode, tc_work[0], tc_work[1],
-                                              shares["rankb_tc"]["ms"],
-                                              shares["rankb_tc"]["launches"], 1)
-    roofline["kernel_shares"] = shares
+    # the sweep-level roofline (class shares from the profiled step); the
+    # dominant kernel's figures from its events over the timed region
+    if dominant:
+        k_launches, k_ms = _lib.ld_profile_query(dominant)
+        k_bytes, k_flops = _lib.ld_profile_work(dominant)
+        shares[dominant].update({"launches": k_launches / args.steps, "ms": k_ms / args.steps,
+                                 "bytes": k_bytes / args.steps, "flops": k_flops / args.steps,
+                                 "timed_region": True})
+    roofline = sweep_roofline(mode, N, ms_max, shares)
+    roofline["dominant_kernel"] = dominant
 
     # end to end: pinned host input -> device -> sweep -> host result, per step
-    A_host = torch.from_numpy(A_np).pin_memory()
-    A_dev = torch.empty_like(A)
     import ctypes
+    A_host = A.cpu().pin_memory()
+    A_dev = torch.empty_like(A)
     hs, hl = ctypes.c_double(), ctypes.c_double()
     mcode = _lib.MODES[mode]
+    dcode = _lib.LD_DTYPE_F64 if A.dtype == torch.float64 else _lib.LD_DTYPE_F32
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         A_dev.copy_(A_host, non_blocking=True)
-        code = _lib.ld_logdet(A_dev.data_ptr(), _lib.LD_DTYPE_F64, N, N, mcode,
-                              stream.cuda_stream, ctypes.addressof(hs), ctypes.addressof(hl))
+        code = _lib.ld_logdet(A_dev.data_ptr(), dcode, N, N, mcode, stream.cuda_stream,
+                              ctypes.addressof(hs), ctypes.addressof(hl))
         _lib.check("ld_logdet", code)
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
@@ -399,14 +522,27 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": world * flops(N) / float(te[0]) / 1e12, "unit": UNIT,
-           "h2d_bytes_per_step": A_np.nbytes, "d2h_bytes_per_step": 16}
+           "h2d_bytes_per_step": A_host.numel() * A_host.element_size(), "d2h_bytes_per_step": 16}
+    del A_host, A_dev
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(A_np, target_s=args.cpu_seconds)
+        try:
+            A_np = host_matrix(args.workload, N) if args.workload in ("dense", "spdcov8000") \
+                else A.cpu().double().numpy()
+            cpu = oracle_sample(A_np, target_s=args.cpu_seconds,
+                                what=WORKLOADS[args.workload][1].split(";")[0])
+            del A_np
+            if N > 8000:
+                import workloads
+                cpu["full_sweep_n8000"] = oracle_full_sweep(
+                    workloads.dense_gaussian(8000, seed=1, var=1.0 / 8000),
+                    what="dense iid N(0,1/N) matrix of seed 1 (context: a whole sweep)")
+        except Exception as ex:
+            cpu = {"error": str(ex)[:200]}
     paths = None
     if rank == 0 and not args.no_paths:
-        paths = other_paths(pk, _lib, A, mode, dev, err_gold=gold)
+        paths = other_paths(pk, _lib, dev, args.workload, mode, A, ref)
 
     if rank == 0:
         line = {
@@ -414,7 +550,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE.get(mode, mode), "data": "synthetic",
-            "config": {"workload": f"dense iid N(0,1/N) N={N} seed {SEED}, one sweep per step",
+            "config": {"workload": WORKLOADS[args.workload][1] + ", one sweep per step",
                        "N": N, "mode": mode, "parallelism": "replicas" if world > 1 else "1 gpu",
                        "l2": "inputs larger than L2 (N^2 elements > 129 MB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -427,13 +563,13 @@ def run_ours(args):
     return 0
 
 
-def run_other_workload(args, pk, _lib, dev, stream, rank, world):
-    """The batched (4096 covariance matrices) and gradient (256 x 1024^2) workloads
-    as their own benchmark line (units: dets/s and matrices/s)."""
+def other_workload_line(workload, pk, _lib, dev, warmup, steps, world=1, full=False):
+    """The batched (4096 covariance matrices) and gradient (256 x 1024^2)
+    workloads (units: dets/s and matrices/s), with their own rooflines."""
     import torch
     import torch.distributed as dist
     import workloads
-    if args.workload == "batched4096":
+    if workload == "batched4096":
         sizes = workloads.batched_sizes(4096, seed=3)
         mats = workloads.batched_covariances_torch(sizes, seed=3, device=dev)
         batch = pk.BatchedInputs(mats)
@@ -464,24 +600,12 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
         wl = ("256 SPD 1024x1024 FP32, eigenvalues log-uniform in [1e-2,1], seed 4: log|det| "
               "(batched blocked sweep, 3xTF32) + gradient")
         flop = B * (2.0 * n ** 3 / 3.0 + 2.0 * n ** 3)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
-    _lib.ld_profile_start(None)
-    step()
-    torch.cuda.synchronize(dev)
-    _lib.ld_profile_stop()
-    shares = {}
-    for cls in _lib.ld_profile_classes():
-        nl, tms = _lib.ld_profile_query(cls)
-        shares[cls] = {"launches": nl, "ms": round(tms, 4)}
-    tc_work = None
-    if args.workload != "batched4096" and shares:
-        # the roofline follows the kernel with the largest share; the tensor-core
-        # update (same profiled step, its own event time) is reported beside it
+    shares = profile_step(_lib, step, dev)
+    if workload != "batched4096" and shares:
         kernel = max(shares, key=lambda k: shares[k]["ms"])
-        if "rankb_tc" in shares and kernel != "rankb_tc":
-            tc_work = _lib.ld_profile_work("rankb_tc")
     clocks = ClockSampler(dev.index or 0)
     _lib.ld_profile_start(kernel)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -491,58 +615,58 @@ def run_other_workload(args, pk, _lib, dev, stream, rank, world):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
+    e0.record()
+    for _ in range(steps):
         step()
-    e1.record(stream)
+    e1.record()
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     _lib.ld_profile_stop()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     if world > 1:
         tm = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms = float(tm[0])
     launches_all, _ = _lib.ld_profile_query(None)
     k_launches, k_ms = _lib.ld_profile_query(kernel)
-    peaks = read_peaks()
-    # the FP32 SIMT FMA peak: 152 SMs x 128 FMA/clk x 2 flop at the sampled SM clock
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    k_flop = flop * args.steps if args.workload == "batched4096" else None
     roof = None
-    if args.workload != "batched4096" and k_ms > 0:
-        kb, kf = _lib.ld_profile_work(kernel)
-        roof = make_roofline(kernel, "f32_3xtf32", kb, kf, k_ms, k_launches, args.steps)
-        if tc_work:
-            roof["secondary"] = make_roofline("rankb_tc", "f32_3xtf32", tc_work[0], tc_work[1],
-                                              shares["rankb_tc"]["ms"],
-                                              shares["rankb_tc"]["launches"], 1)
-        roof["kernel_shares"] = shares
-    if k_flop and k_ms > 0:
-        ach = k_flop / (k_ms * 1e-3) / 1e12
+    if workload == "batched4096" and k_ms > 0:
+        # the FP32 SIMT FMA peak: SMs x 128 FMA/clk x 2 flop at the sampled SM clock
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = flop * steps / (k_ms * 1e-3) / 1e12
+        tr = NCU_TRAFFIC.get(("batched", "batched4096"))
         roof = {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": ach / alu_peak,
-                "traffic": NCU_TRAFFIC[("batched", "batched4096")]["bytes"],
-                "traffic_note": "ncu, one launch: " + NCU_TRAFFIC[("batched", "batched4096")]["launch"],
-                "peak_note": "FP32 FMA: SMs x 128 lanes x 2 flop x sampled SM clock",
-                "kernel_shares": shares}
+                "traffic": tr["bytes"] if tr else None,
+                "traffic_note": ("ncu, one launch: " + tr["launch"]) if tr else None,
+                "peak_note": "FP32 FMA: SMs x 128 lanes x 2 flop x sampled SM clock"}
+    elif k_ms > 0:
+        kb, kf = _lib.ld_profile_work(kernel)
+        roof = make_roofline(kernel, "f32_3xtf32", kb, kf, k_ms, k_launches, steps)
+        if "rankb_tc" in shares and kernel != "rankb_tc":
+            s = shares["rankb_tc"]
+            roof["tensor_update"] = make_roofline("rankb_tc", "f32_3xtf32", s["bytes"], s["flops"],
+                                                  s["ms"], s["launches"], 1)
+    if roof is not None:
+        roof["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
+                                 for k, v in shares.items()}
     value = world * units / (ms * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+    res = {"value": value, "unit": unit, "ms_per_step": ms, "tflops": flop / (ms * 1e-3) / 1e12,
+           "workload": wl, "roofline": roof or {"kernel_shares": shares}}
+    if workload == "batched4096":
+        res["dets_per_s"] = value
+    if not full:
+        return res
+    return {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl, "l2": "inputs larger than L2"},
-            "roofline": roof or {"kernel_shares": shares}, "tflops": flop / (ms * 1e-3) / 1e12,
-            "gpu_launches": launches_all, "clocks": clk, "cpu_baseline": None,
-            "e2e": None}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+            "roofline": res["roofline"], "tflops": res["tflops"],
+            "gpu_launches": launches_all, "clocks": clk, "cpu_baseline": None, "e2e": None}
 
 
 def main():
@@ -552,13 +676,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f32_3xtf32")
-    ap.add_argument("--N", type=int, default=N_DEFAULT)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="spd32768",
+                    choices=sorted(WORKLOADS) + ["batched4096", "grad256x1024"])
+    ap.add_argument("--N", type=int, default=None, help="size (dense workload only)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched4096", "grad256x1024"])
     args = ap.parse_args()
+    if args.N is not None and args.workload != "dense":
+        ap.error("--N applies to the dense workload only")
     if args.impl == "reference":
+        if args.workload in ("batched4096", "grad256x1024"):
+            ap.error("the reference arm times the single-matrix workloads")
         return run_reference(args)
     return run_ours(args)
 

@@ -81,11 +81,51 @@ typedef enum {
 ld_status ld_logdet(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
                     void* stream, double* sign, double* logabs);
 
+/* Pivot-column rule of a sweep (Sec. 2.2 and the earlier work named in Sec. 1). */
+typedef enum {
+  LD_PIVOT_MAX_ABS = 0,        /* largest |a_kj|, ties to the smallest original label
+                                  (the paper's rule, Sec. 2.2; every other entry point) */
+  LD_PIVOT_CLOSEST_TO_ONE = 1, /* the nonzero entry whose |a_kj| is closest to 1 */
+  LD_PIVOT_FIRST_NONZERO = 2   /* the nonzero entry of the smallest original label */
+} ld_pivot_rule;
+
+/* Which line the pivot is factored out of (Eq. (3), Sec. 2.3). */
+typedef enum {
+  LD_FACTOR_ROW = 0,   /* r_j = a_kj / a_kl, minors a_ij - a_il r_j (the paper's) */
+  LD_FACTOR_COLUMN = 1 /* c_i = a_il / a_kl, minors a_ij - c_i a_kj */
+} ld_factor_side;
+
+/*
+ * ld_logdet_variant - ld_logdet with the pivot-column rule and the factoring
+ * side chosen by the caller (Sec. 1 names the rules of earlier work; Sec. 2.3
+ * shows that factoring the pivot out of row k or column l gives the same
+ * determinant). Sec. 2.2 argues that the closest-to-1 rule can overflow where
+ * the largest |a_kj| does not; this entry point lets a caller see that.
+ *   mode   LD_F64_PLAIN or LD_F32_PLAIN for any rule and side; every other mode
+ *          only with LD_PIVOT_MAX_ABS and LD_FACTOR_ROW (then it is ld_logdet),
+ *          else LD_ERR_UNSUPPORTED
+ *   rule, side  as above; an unknown value gives LD_ERR_INVALID_ARG
+ *   factors  NULL, or a factor record of ld_factors_size(n, mode) bytes (256-B
+ *            aligned) that receives the sweep's record as ld_logdet_factor
+ *            writes it: colperm, pivpos and pivval give the pivot sequence under
+ *            the chosen rule. With LD_FACTOR_COLUMN the record's F holds the
+ *            column-factored form (pivot rows unscaled, multipliers divided by
+ *            their pivot) and the header's side field is 1; ld_logdet_backward
+ *            accepts only row-factored records (LD_ERR_UNSUPPORTED otherwise)
+ * Ties under every rule go to the smallest original column label. The other
+ * arguments, outputs and errors are those of ld_logdet. FP64 storage takes its
+ * decisions in FP64, FP32 storage in FP32.
+ */
+ld_status ld_logdet_variant(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda,
+                            ld_mode mode, ld_pivot_rule rule, ld_factor_side side, void* stream,
+                            void* factors, double* sign, double* logabs);
+
 /*
  * ld_factors_size - bytes of the factor record that ld_logdet_factor writes for
  * an n x n matrix in `mode` (0 for an invalid request). The record is
  *   [0, 256)            header: int64 n, int64 ldf, int32 mode, int32 flags,
- *                       double sign, double logabs (rest reserved)
+ *                       double sign, double logabs, int32 side (0: pivots factored
+ *                       out of their rows, 1: out of their columns; rest reserved)
  *   [256, +n*ldf*es)    F: n x ldf row-major, es = 8 (F64 modes) or 4 (F32 modes)
  *   then int32 colperm[n], int32 pivpos[n], double pivval[n] (each 256-B aligned)
  * F holds the packed Crout factors in the swap-to-boundary layout: the column
@@ -231,15 +271,54 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
                             double* sign, double* logabs);
 
 /*
- * Tuning table used by the launchers (process-wide; the autotuner in the Python
- * package sets it from timings, see paper_1811_08057_gb300/tune.py):
- *   "blocked_b"       panel width b of the blocked sweep: 64 or 128 (default 128)
- *   "batched_kb_<k>"  panels of the batched sweep for matrices with n in
- *                     [64k, 64k+63] (k = 0..8; k = 8 also covers larger n): 8 or 16
- * LD_ERR_INVALID_ARG for an unknown name or value.
+ * Tuning table used by the launchers (process-wide; ld_tune sets it from timings):
+ *   "blocked_b"           panel width b of the blocked sweep: 64 or 128 (default 128)
+ *   "blocked_pair_min_n"  from this n on (default 16384), FP32 blocked sweeps pair
+ *                         the trailing updates of two panels (one update with
+ *                         K = 2b instead of two with K = b for the rows past the
+ *                         next panel; exact arithmetic unchanged); >= 0
+ *   "batched_kb_<k>"      panels of the batched sweep for matrices with n in
+ *                         [64k, 64k+63] (k = 0..8; k = 8 also covers larger n): 8 or 16
+ *   "wait_limit_ns"       limit of the bounded waits of the grid-wide panel kernel
+ *                         (LD_F64_BLOCKED's panels) on the current device, >= 0,
+ *                         default 1e9; a wait that runs out flags the sweep, its
+ *                         results become NaN and the call returns LD_ERR_TIMEOUT
+ *                         (when it reads its results back). Not in the tune file.
+ *                         The cluster panel and the tensor-core kernels keep a
+ *                         fixed 1 s: their timeout paths are not meant to be
+ *                         provoked (asynchronous copies could still be in flight)
+ * LD_ERR_INVALID_ARG for an unknown name or value. The first call into the
+ * table (or the first launch that reads it) loads $LD_TUNE_CACHE/<GPU name>.tune
+ * if that variable names a directory holding such a file.
  */
 ld_status ld_set_tuning(const char* name, int64_t value);
 ld_status ld_get_tuning(const char* name, int64_t* value);
+
+/*
+ * ld_tune - the autotuner (no counterpart in the paper: a deployment aid). Times
+ * the candidate settings on synthetic matrices (a_ij = u_ij / sqrt(n) +
+ * 2 [i == j], u_ij uniform in [-1, 1) from a counter-based hash) of the given
+ * sizes in `mode`, applies the fastest to the tuning table and, if
+ * $LD_TUNE_CACHE is set, stores the table as $LD_TUNE_CACHE/<GPU name>.tune.
+ *   sizes   host array of `count` matrix sizes the caller will run
+ *   mode    blocked modes: b in {64, 128} x paired updates on or off, timed on
+ *           one matrix of the largest size (at most 32768); LD_F32_PLAIN /
+ *           LD_F64_PLAIN: the batched panel depth {8, 16} of every size class
+ *           present, timed on up to 256 matrices of the class's largest size
+ * Allocates stream-ordered scratch, runs sweeps on `stream` and waits for them.
+ * LD_ERR_INVALID_ARG for NULL sizes, count <= 0, a negative size or an unknown
+ * mode; on any other error the table is left as it was.
+ */
+ld_status ld_tune(const int64_t* sizes, int64_t count, ld_mode mode, void* stream);
+
+/*
+ * ld_tune_save / ld_tune_load - the tuning table as a text file of
+ * "name value" lines. path NULL means $LD_TUNE_CACHE/<GPU name>.tune. A load
+ * checks every line before applying any: a bad name or value (or an unreadable
+ * file) gives LD_ERR_INVALID_ARG and leaves the table unchanged.
+ */
+ld_status ld_tune_save(const char* path);
+ld_status ld_tune_load(const char* path);
 
 /* Human-readable name of a status code (static storage). */
 const char* ld_status_string(ld_status s);

@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     ld_logdet_backward,
     ld_logdet_batched,
     ld_logdet_factor,
+    ld_logdet_variant,
     ld_status_string,
     ld_version,
     load,
@@ -33,5 +34,7 @@ from .api import (  # noqa: F401
     logdet,
     logdet_batched,
     logdet_factor,
+    logdet_variant,
+    logdet_variant_factor,
     parse_factors,
 )

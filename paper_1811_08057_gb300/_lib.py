@@ -30,6 +30,9 @@ MODES = {
     "f32_3xtf32": LD_F32_3XTF32,
     "f32_bf16x3": LD_F32_BF16X3,
 }
+# ld_pivot_rule, ld_factor_side
+PIVOT_RULES = {"max_abs": 0, "closest_to_one": 1, "first_nonzero": 2}
+FACTOR_SIDES = {"row": 0, "column": 1}
 # ld_dtype
 LD_DTYPE_F64 = 0
 LD_DTYPE_F32 = 1
@@ -46,6 +49,7 @@ _pd = ctypes.c_void_p  # double* (host or device address as an integer)
 SIGNATURES = {
     "ld_logdet": ([_vp, _int, _i64, _i64, _int, _vp, _pd, _pd], _int),
     "ld_factors_size": ([_i64, _int], _sz),
+    "ld_logdet_variant": ([_vp, _int, _i64, _i64, _int, _int, _int, _vp, _vp, _pd, _pd], _int),
     "ld_logdet_factor": ([_vp, _int, _i64, _i64, _int, _vp, _vp, _pd, _pd], _int),
     "ld_logdet_backward": ([_vp, _vp, _vp, _i64, _vp], _int),
     "ld_logdet_batched": ([_vp, _int, _vp, _vp, _i64, _i64, _int, _vp, _vp, _vp], _int),
@@ -60,6 +64,9 @@ SIGNATURES = {
     "ld_profile_work": ([ctypes.c_char_p, _vp, _vp], _int),
     "ld_profile_classes": ([_vp, _i64], _int),
     "ld_set_tuning": ([ctypes.c_char_p, _i64], _int),
+    "ld_tune": ([_vp, _i64, _int, _vp], _int),
+    "ld_tune_save": ([ctypes.c_char_p], _int),
+    "ld_tune_load": ([ctypes.c_char_p], _int),
     "ld_get_tuning": ([ctypes.c_char_p, _vp], _int),
     "ld_status_string": ([_int], ctypes.c_char_p),
     "ld_version": ([], ctypes.c_char_p),
@@ -112,6 +119,11 @@ def check(func: str, code: int):
 # Same-name thin wrappers (integers are device/host addresses).
 def ld_logdet(A, a_dtype, n, lda, mode, stream, sign, logabs) -> int:
     return load().ld_logdet(A, a_dtype, n, lda, mode, stream, sign, logabs)
+
+
+def ld_logdet_variant(A, a_dtype, n, lda, mode, rule, side, stream, factors, sign, logabs) -> int:
+    return load().ld_logdet_variant(A, a_dtype, n, lda, mode, rule, side, stream, factors, sign,
+                                    logabs)
 
 
 def ld_factors_size(n, mode) -> int:
@@ -192,6 +204,20 @@ def ld_get_tuning(name: str) -> int:
     v = ctypes.c_int64()
     check("ld_get_tuning", load().ld_get_tuning(name.encode(), ctypes.addressof(v)))
     return v.value
+
+
+def ld_tune(sizes, mode, stream=None) -> int:
+    """Autotunes the table for these matrix sizes (a list of ints) in `mode`."""
+    arr = (ctypes.c_int64 * len(sizes))(*[int(x) for x in sizes])
+    return load().ld_tune(ctypes.addressof(arr), len(sizes), mode, stream)
+
+
+def ld_tune_save(path=None) -> int:
+    return load().ld_tune_save(path.encode() if path else None)
+
+
+def ld_tune_load(path=None) -> int:
+    return load().ld_tune_load(path.encode() if path else None)
 
 
 def ld_status_string(code) -> str:

@@ -54,6 +54,48 @@ def logdet(A: torch.Tensor, mode="f64_plain", stream=None):
     return out[0], out[1]
 
 
+def logdet_variant(A: torch.Tensor, mode="f64_plain", rule="max_abs", factor="row",
+                   stream=None):
+    """(sign, log|det A|) with another pivot-column rule ("max_abs", the paper's;
+    "closest_to_one" or "first_nonzero", earlier work) or the pivot factored out
+    of the "column" instead of the "row"; plain modes only for anything but the
+    paper's choices."""
+    _check_matrix(A)
+    if rule not in _lib.PIVOT_RULES or factor not in _lib.FACTOR_SIDES:
+        raise ValueError(f"unknown rule {rule!r} or factor side {factor!r}")
+    n = A.shape[0]
+    lda = max(A.stride(0), 1) if n > 0 else 1
+    out = torch.empty(2, dtype=torch.float64, device=A.device)
+    code = _lib.ld_logdet_variant(A.data_ptr(), _dtype_code(A), n, lda, _mode_code(mode),
+                                  _lib.PIVOT_RULES[rule], _lib.FACTOR_SIDES[factor],
+                                  _stream_handle(stream), 0, out.data_ptr(), out.data_ptr() + 8)
+    _lib.check("ld_logdet_variant", code)
+    return out[0], out[1]
+
+
+def logdet_variant_factor(A: torch.Tensor, mode="f64_plain", rule="max_abs", factor="row",
+                          stream=None) -> Factors:
+    """As logdet_variant, and keeps the factor record (its pivot sequence under the
+    chosen rule; with factor="column" F holds the column-factored form)."""
+    _check_matrix(A)
+    if rule not in _lib.PIVOT_RULES or factor not in _lib.FACTOR_SIDES:
+        raise ValueError(f"unknown rule {rule!r} or factor side {factor!r}")
+    n = A.shape[0]
+    lda = max(A.stride(0), 1) if n > 0 else 1
+    mode = _mode_code(mode)
+    size = _lib.ld_factors_size(n, mode)
+    record = torch.empty(size + 256, dtype=torch.uint8, device=A.device)
+    shift = (-record.data_ptr()) % 256
+    record = record[shift:shift + size]
+    out = torch.empty(2, dtype=torch.float64, device=A.device)
+    code = _lib.ld_logdet_variant(A.data_ptr(), _dtype_code(A), n, lda, mode,
+                                  _lib.PIVOT_RULES[rule], _lib.FACTOR_SIDES[factor],
+                                  _stream_handle(stream), record.data_ptr(), out.data_ptr(),
+                                  out.data_ptr() + 8)
+    _lib.check("ld_logdet_variant", code)
+    return parse_factors(record, n, mode)
+
+
 @dataclass
 class Factors:
     """A factor record (see ld_factors_size in include/logdet.h) and its views."""

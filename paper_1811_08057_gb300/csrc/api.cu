@@ -61,11 +61,75 @@ bool is_device_pointer(const void* ptr) {
 // ---- tuning table (process-wide; set by ld_set_tuning, read by the launchers) ----
 namespace {
 int g_blocked_b = 128;              // panel width of the blocked sweep (64 or 128)
+int64_t g_pair_min_n = 16384;       // pair the trailing updates of two panels from this n
 int g_batched_kb[kTuneBuckets] = {16, 16, 16, 16, 16, 16, 16, 16, 16};
 }  // namespace
 
-int tuned_blocked_b() { return g_blocked_b; }
-const int* tuned_batched_kb() { return g_batched_kb; }
+int tuned_blocked_b() {
+  tune_cache_autoload();
+  return g_blocked_b;
+}
+int64_t tuned_pair_min_n() {
+  tune_cache_autoload();
+  return g_pair_min_n;
+}
+const int* tuned_batched_kb() {
+  tune_cache_autoload();
+  return g_batched_kb;
+}
+
+ld_status tuning_set(const char* name, int64_t value) {
+  if (!name) return LD_ERR_INVALID_ARG;
+  if (strcmp(name, "blocked_b") == 0) {
+    if (value != 64 && value != 128) return LD_ERR_INVALID_ARG;
+    g_blocked_b = (int)value;
+    return LD_OK;
+  }
+  if (strcmp(name, "blocked_pair_min_n") == 0) {
+    if (value < 0) return LD_ERR_INVALID_ARG;
+    g_pair_min_n = value;
+    return LD_OK;
+  }
+  if (strcmp(name, "wait_limit_ns") == 0) {
+    if (value < 0) return LD_ERR_INVALID_ARG;
+    return set_panel_wait_limit((uint64_t)value);
+  }
+  if (strncmp(name, "batched_kb_", 11) == 0) {
+    char* end = nullptr;
+    const long k = strtol(name + 11, &end, 10);
+    if (end == name + 11 || *end != 0 || k < 0 || k >= kTuneBuckets || (value != 8 && value != 16))
+      return LD_ERR_INVALID_ARG;
+    g_batched_kb[k] = (int)value;
+    return LD_OK;
+  }
+  return LD_ERR_INVALID_ARG;
+}
+
+ld_status tuning_get(const char* name, int64_t* value) {
+  if (!name || !value) return LD_ERR_INVALID_ARG;
+  if (strcmp(name, "blocked_b") == 0) {
+    *value = g_blocked_b;
+    return LD_OK;
+  }
+  if (strcmp(name, "blocked_pair_min_n") == 0) {
+    *value = g_pair_min_n;
+    return LD_OK;
+  }
+  if (strcmp(name, "wait_limit_ns") == 0) {
+    uint64_t ns = 0;
+    const ld_status st = get_panel_wait_limit(&ns);
+    *value = (int64_t)ns;
+    return st;
+  }
+  if (strncmp(name, "batched_kb_", 11) == 0) {
+    char* end = nullptr;
+    const long k = strtol(name + 11, &end, 10);
+    if (end == name + 11 || *end != 0 || k < 0 || k >= kTuneBuckets) return LD_ERR_INVALID_ARG;
+    *value = g_batched_kb[k];
+    return LD_OK;
+  }
+  return LD_ERR_INVALID_ARG;
+}
 
 static ld_status run_sweep(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                            bool keep, cudaStream_t stream) {
@@ -85,7 +149,7 @@ static ld_status run_sweep(const void* A, ld_dtype a_dtype, int64_t lda, const R
 
 static ld_status logdet_impl(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda,
                              ld_mode mode, void* stream_v, void* factors, double* sign,
-                             double* logabs) {
+                             double* logabs, int rule = 0, int colf = 0) {
   if (n < 0 || lda < (n > 0 ? n : 1) || (n > 0 && !A) || !sign || !logabs)
     return LD_ERR_INVALID_ARG;
   if (!mode_valid(mode) || (a_dtype != LD_DTYPE_F64 && a_dtype != LD_DTYPE_F32))
@@ -103,6 +167,8 @@ static ld_status logdet_impl(const void* A, ld_dtype a_dtype, int64_t n, int64_t
   }
   Record r;
   record_layout(n, mode, base, &r);
+  r.rule = rule;
+  r.colf = colf;
   const bool sign_dev = is_device_pointer(sign);
   const bool log_dev = is_device_pointer(logabs);
   ld_status st = run_sweep(A, a_dtype, lda, r, factors != nullptr, stream);
@@ -130,6 +196,18 @@ extern "C" {
 ld_status ld_logdet(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda, ld_mode mode,
                     void* stream, double* sign, double* logabs) {
   return ld::logdet_impl(A, a_dtype, n, lda, mode, stream, nullptr, sign, logabs);
+}
+
+ld_status ld_logdet_variant(const void* A, ld_dtype a_dtype, int64_t n, int64_t lda,
+                            ld_mode mode, ld_pivot_rule rule, ld_factor_side side, void* stream,
+                            void* factors, double* sign, double* logabs) {
+  if ((int)rule < LD_PIVOT_MAX_ABS || (int)rule > LD_PIVOT_FIRST_NONZERO ||
+      ((int)side != LD_FACTOR_ROW && (int)side != LD_FACTOR_COLUMN) || !ld::mode_valid(mode))
+    return LD_ERR_INVALID_ARG;
+  const bool paper = rule == LD_PIVOT_MAX_ABS && side == LD_FACTOR_ROW;
+  if (!paper && mode != LD_F64_PLAIN && mode != LD_F32_PLAIN) return LD_ERR_UNSUPPORTED;
+  return ld::logdet_impl(A, a_dtype, n, lda, mode, stream, factors, sign, logabs, (int)rule,
+                         (int)side);
 }
 
 size_t ld_factors_size(int64_t n, ld_mode mode) {
@@ -164,34 +242,13 @@ const char* ld_status_string(ld_status s) {
 const char* ld_version(void) { return "liblogdet 0.1 sm_103a"; }
 
 ld_status ld_set_tuning(const char* name, int64_t value) {
-  if (!name) return LD_ERR_INVALID_ARG;
-  if (strcmp(name, "blocked_b") == 0) {
-    if (value != 64 && value != 128) return LD_ERR_INVALID_ARG;
-    ld::g_blocked_b = (int)value;
-    return LD_OK;
-  }
-  if (strncmp(name, "batched_kb_", 11) == 0) {
-    const int k = atoi(name + 11);
-    if (k < 0 || k >= ld::kTuneBuckets || (value != 8 && value != 16)) return LD_ERR_INVALID_ARG;
-    ld::g_batched_kb[k] = (int)value;
-    return LD_OK;
-  }
-  return LD_ERR_INVALID_ARG;
+  ld::tune_cache_autoload();
+  return ld::tuning_set(name, value);
 }
 
 ld_status ld_get_tuning(const char* name, int64_t* value) {
-  if (!name || !value) return LD_ERR_INVALID_ARG;
-  if (strcmp(name, "blocked_b") == 0) {
-    *value = ld::g_blocked_b;
-    return LD_OK;
-  }
-  if (strncmp(name, "batched_kb_", 11) == 0) {
-    const int k = atoi(name + 11);
-    if (k < 0 || k >= ld::kTuneBuckets) return LD_ERR_INVALID_ARG;
-    *value = ld::g_batched_kb[k];
-    return LD_OK;
-  }
-  return LD_ERR_INVALID_ARG;
+  ld::tune_cache_autoload();
+  return ld::tuning_get(name, value);
 }
 
 }  // extern "C"

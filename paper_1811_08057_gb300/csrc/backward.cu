@@ -380,6 +380,7 @@ extern "C" ld_status ld_logdet_backward(const void* factors, const double* g, vo
     return LD_ERR_CUDA;
   if (h.n < 0 || !mode_valid(h.mode) || h.ldf != leading_dim(h.n)) return LD_ERR_INVALID_ARG;
   if (ldg < (h.n > 0 ? h.n : 1)) return LD_ERR_INVALID_ARG;
+  if (h.side != 0) return LD_ERR_UNSUPPORTED;  // a column-factored record (ld_logdet_variant)
   if (h.n == 0) return LD_OK;
   void* scratch = nullptr;
   ld_status st = scratch_alloc(&scratch, 2 * kAlign, stream);

@@ -621,6 +621,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
         h->n = n;
         h->ldf = ldw;
         h->mode = args.mode;
+        h->side = 0;
       }
     }
     if (sizeof(T) == 8 && tid == 0) {
@@ -642,6 +643,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
         h->n = n;
         h->ldf = ldw;
         h->mode = args.mode;
+        h->side = 0;
         h->flags = flags;
         h->sign = sg;
         h->logabs = la;

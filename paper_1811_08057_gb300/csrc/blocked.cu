@@ -217,6 +217,32 @@ __global__ void transpose_rows_kernel(const T* __restrict__ F, int64_t ldf, int 
   }
 }
 
+// Rows of an operand buffer (rows of row_bytes, hi and optional lo part)
+// permuted by a panel's move list: row dst receives row src for every (dst, src)
+// pair. Phase 0 copies the source rows into tmp, phase 1 writes them to their
+// destinations (two launches, so every source is read before any row changes).
+// One warp per pair.
+__global__ void permute_rows_kernel(char* __restrict__ hi, char* __restrict__ lo, int row_bytes,
+                                    const int* __restrict__ moves, uint4* __restrict__ tmp,
+                                    int phase) {
+  const int nm = moves[0];
+  const int pair = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pair >= nm) return;
+  const int dst = moves[1 + 2 * pair], src = moves[2 + 2 * pair];
+  const int nchunk = row_bytes / 16;
+  for (int part = 0; part < (lo ? 2 : 1); ++part) {
+    char* base = part ? lo : hi;
+    uint4* t = tmp + ((size_t)pair * 2 + part) * nchunk;
+    for (int c = lane; c < nchunk; c += 32) {
+      if (phase == 0)
+        t[c] = reinterpret_cast<const uint4*>(base + (size_t)src * row_bytes)[c];
+      else
+        reinterpret_cast<uint4*>(base + (size_t)dst * row_bytes)[c] = t[c];
+    }
+  }
+}
+
 // ------------------------------------------------------ batched blocked sweep
 // Stage of matrix blockIdx.z into its record (FP32 storage): F = A (any input
 // type and lda), colperm = identity, sweep state reset, header size fields. A
@@ -234,6 +260,7 @@ __global__ void stage_batched_kernel(const void* const* __restrict__ A_ptrs, int
     h->n = n;
     h->ldf = ldf;
     h->mode = mode;
+    h->side = 0;
     st->sign = 1.0;
     st->sum = 0.0;
     st->comp = 0.0;
@@ -464,6 +491,28 @@ ld_status trailing_update(ld_mode mode, int64_t M, int64_t ncols, int64_t bb, co
                   err, stream);
 }
 
+// The B operand rows (positions) of an earlier panel follow a later panel's
+// column moves. tmp: 2 * kPanel * 2 rows of bb elements.
+ld_status permute_operand_rows(const OpBuf& bo, int64_t bb, const int* moves, void* tmp,
+                               cudaStream_t stream) {
+  const int row_bytes = (int)(bb * bo.es);
+  if (row_bytes % 16 != 0) return LD_ERR_UNSUPPORTED;
+  const unsigned grid = (unsigned)ceil_div(2 * kPanel * 32, 256);
+  ProfScope ps("permute", stream, 4.0 * 2 * kPanel * row_bytes, 0.0);
+  for (int phase = 0; phase < 2; ++phase) {
+    permute_rows_kernel<<<grid, 256, 0, stream>>>(bo.hi, bo.lo, row_bytes, moves,
+                                                  static_cast<uint4*>(tmp), phase);
+    if (cudaGetLastError() != cudaSuccess) return LD_ERR_CUDA;
+  }
+  return LD_OK;
+}
+
+// Rows [r0, r0 + rows) of an operand buffer of bb-element rows.
+TcOperand op_rows(const OpBuf& o, int64_t r0, int64_t bb) {
+  const size_t off = (size_t)r0 * bb * o.es;
+  return TcOperand{o.hi + off, o.lo ? o.lo + off : nullptr, bb, 0};
+}
+
 template <typename T>
 ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r, bool keep,
                         cudaStream_t stream) {
@@ -472,27 +521,6 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   ld_status st = launch_stage<T>(A, a_dtype, lda, r, stream);
   if (st != LD_OK || n == 0) return st;
   const size_t es = sizeof(T);
-  const size_t grid_panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
-  const size_t cl_bytes = align_up(panel_cluster_scratch_bytes(), kAlign);
-  const size_t opb = op_bytes(r.mode, n, b);
-  // A and B operands double-buffered by panel parity: the low-priority stream
-  // may still read step k's while the critical stream writes step k+1's
-  const size_t scratch_bytes = grid_panel_bytes + 2 * cl_bytes + 4 * opb + 2 * kAlign;
-  void* scratch = nullptr;
-  st = scratch_alloc(&scratch, scratch_bytes, stream);
-  if (st != LD_OK) return st;
-  char* p = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
-  void* panel_scratch = p;
-  p += grid_panel_bytes;
-  char* cl_scratch[2] = {p, p + cl_bytes};
-  p += 2 * cl_bytes;
-  OpBuf abuf[2], bbuf[2];
-  for (int q = 0; q < 2; ++q) {
-    abuf[q] = op_buf(r.mode, p, n, b);
-    p += opb;
-    bbuf[q] = op_buf(r.mode, p, n, b);
-    p += opb;
-  }
   // LD_PANEL=grid selects the grid-wide panel kernel instead of the cluster one
   const char* pk = getenv("LD_PANEL");
   const bool no_cluster = pk && pk[0] == 'g';
@@ -500,6 +528,41 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   // kernels restricted to the panel rows) instead of the persistent panel kernel
   const char* pp = getenv("LD_PANEL_PER_PIVOT");
   const bool per_pivot = pp && pp[0] == '1';
+  // Paired updates (FP32 storage, cluster panels, n >= the tuned bound): the
+  // trailing rows beyond the next panel take only the moves and multipliers of
+  // an even panel; the next (odd) step updates them with both panels at once,
+  // K = 2b, which halves the trailing matrix's read-modify-write passes.
+  bool pair = sizeof(T) == 4 && !per_pivot && !no_cluster && b == kPanel &&
+              n >= tuned_pair_min_n();
+  const int nbuf = pair ? 4 : 2;
+  const size_t grid_panel_bytes = align_up(panel_scratch_bytes(2 * device_sm_count(), es), kAlign);
+  const size_t cl_bytes = align_up(panel_cluster_scratch_bytes(), kAlign);
+  const size_t opb = op_bytes(r.mode, n, b);
+  const size_t perm_bytes = pair ? align_up((size_t)2 * kPanel * 2 * kPanel * 4, kAlign) : 0;
+  // A and B operands by panel parity (by step modulo 4 when pairing): the
+  // low-priority stream may still read earlier steps' while the critical stream
+  // writes the current one's
+  const size_t scratch_bytes =
+      grid_panel_bytes + nbuf * cl_bytes + 2 * nbuf * opb + perm_bytes + 2 * kAlign;
+  void* scratch = nullptr;
+  st = scratch_alloc(&scratch, scratch_bytes, stream);
+  if (st != LD_OK) return st;
+  char* p = reinterpret_cast<char*>(align_up(reinterpret_cast<uintptr_t>(scratch), kAlign));
+  void* panel_scratch = p;
+  p += grid_panel_bytes;
+  char* cl_scratch[4] = {};
+  for (int q = 0; q < nbuf; ++q) {
+    cl_scratch[q] = p;
+    p += cl_bytes;
+  }
+  OpBuf abuf[4], bbuf[4];
+  for (int q = 0; q < nbuf; ++q) {
+    abuf[q] = op_buf(r.mode, p, n, b);
+    p += opb;
+    bbuf[q] = op_buf(r.mode, p, n, b);
+    p += opb;
+  }
+  void* perm_tmp = p;
   T* F = static_cast<T*>(r.F);
   int* err = &r.state->flags;
   // streams and events of the pipeline (everything on the caller's stream when
@@ -520,7 +583,7 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   for (int64_t s0 = 0, k = 0; s0 < n && st == LD_OK; s0 += b, ++k) {
     const int64_t bb = std::min<int64_t>(b, n - s0);
     const int64_t m0 = n - s0;
-    const int par = (int)(k & 1);
+    const int par = (int)(pair ? (k & 3) : (k & 1));
     const int* moves = reinterpret_cast<const int*>(cl_scratch[par]);  // the panel's move list
     bool used_cluster = false;
     ld_status pst = LD_ERR_UNSUPPORTED;
@@ -555,6 +618,89 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     st = pst;
     const int64_t rows = n - s0 - bb;
     if (st != LD_OK || rows <= 0) continue;
+    // the paired schedule needs the cluster panel's move list: without a cluster
+    // at the first panel the sweep runs unpaired
+    if (pair && k == 0 && !used_cluster) pair = false;
+    if (pair) {
+      if (!used_cluster) {
+        st = LD_ERR_UNSUPPORTED;
+        break;
+      }
+      const OpBuf& ab = abuf[par];
+      const OpBuf& bo = bbuf[par];
+      float* Ff = reinterpret_cast<float*>(F);
+      if ((k & 1) == 0) {
+        // even step: the next panel's rows (brought up to date on hi in the
+        // previous step) get moves, multipliers and this panel's update now; the
+        // rows beyond get moves and multipliers only
+        const int64_t nb = std::min<int64_t>(b, rows);
+        const int64_t rest = rows - nb;
+        st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb, s0 + bb + nb, ab, moves, hi);
+        if (st == LD_OK) st = launch_transpose<T>(r.mode, F, r.ldf, s0, bb, rows, bo, hi);
+        if (st == LD_OK && rest > 0) {
+          OpBuf arest = ab;
+          arest.hi += (size_t)nb * bb * arest.es;
+          if (arest.lo) arest.lo += (size_t)nb * bb * arest.es;
+          st = link(hi, lo, ev[1]);
+          if (st == LD_OK)
+            st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb + nb, n, arest, moves, lo);
+          rest_pending = true;
+        }
+        if (st == LD_OK)
+          st = rankb_tc(r.mode, op_rows(ab, 0, bb), op_rows(bo, 0, bb), (int)nb, (int)rows, (int)bb,
+                        Ff + (s0 + bb) * r.ldf, r.ldf, 0, 1, err, hi);
+        if (st != LD_OK) break;
+        continue;
+      }
+      // odd step: every trailing row holds the previous panel's moves and
+      // multipliers but not its update. The previous panel's B rows follow this
+      // panel's moves; then, per row group (the next two panels' rows on hi, the
+      // rest on lo): this panel's moves, the previous panel's update of the
+      // columns this panel eliminated (now the last bb positions), the
+      // multipliers, and one update with both panels (K = 2b) of the rest.
+      const int pq = (int)((k + 3) & 3);  // buffers of step k - 1
+      const OpBuf& ap = abuf[pq];
+      const OpBuf& bp = bbuf[pq];
+      if (rest_pending) {
+        st = link(lo, hi, ev[2]);
+        rest_pending = false;
+        if (st != LD_OK) break;
+      }
+      st = permute_operand_rows(bp, bb, moves, perm_tmp, hi);
+      if (st == LD_OK) st = launch_transpose<T>(r.mode, F, r.ldf, s0, bb, rows, bo, hi);
+      if (st != LD_OK) break;
+      const int64_t nq = std::min<int64_t>(2 * b, rows);
+      const int64_t far = rows - nq;
+      if (far > 0) {
+        st = link(hi, lo, ev[1]);
+        if (st != LD_OK) break;
+        rest_pending = true;
+      }
+      // group g: rows [g0, g0 + gm) of the trailing block, on stream sg
+      for (int g = 0; g < 2 && st == LD_OK; ++g) {
+        const int64_t g0 = g == 0 ? 0 : nq;
+        const int64_t gm = g == 0 ? nq : far;
+        if (gm <= 0) continue;
+        cudaStream_t sg = g == 0 ? hi : lo;
+        const int64_t row_a = s0 + bb + g0;  // first row of the group
+        st = launch_apply_moves(Ff, r.ldf, row_a, row_a + gm, moves, sg);
+        // rows of step k-1's A operand start at that step's first trailing row (s0)
+        if (st == LD_OK)
+          st = rankb_tc(r.mode, op_rows(ap, bb + g0, bb), op_rows(bp, rows, bb), (int)gm, (int)bb,
+                        (int)bb, Ff + row_a * r.ldf + rows, r.ldf, 0, 1, err, sg);
+        OpBuf ag = ab;
+        ag.hi += (size_t)g0 * bb * ag.es;
+        if (ag.lo) ag.lo += (size_t)g0 * bb * ag.es;
+        if (st == LD_OK)
+          st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, row_a, row_a + gm, ag, nullptr, sg);
+        if (st == LD_OK && rows > 0)
+          st = rankb_tc2(r.mode, op_rows(ap, bb + g0, bb), op_rows(bp, 0, bb), (int)bb,
+                         op_rows(ab, g0, bb), op_rows(bo, 0, bb), (int)bb, (int)gm, (int)rows,
+                         Ff + row_a * r.ldf, r.ldf, err, sg);
+      }
+      if (st != LD_OK) break;
+      continue;
+    }
     const int64_t nb = std::min<int64_t>(b, rows);  // rows of the next panel
     const int64_t rest = rows - nb;
     const int64_t ncols = rows;

@@ -46,16 +46,34 @@ __device__ __forceinline__ void cand_init(Cand& c) {
   c.pad = 0;
 }
 
-__device__ __forceinline__ bool cand_better(double absv, int label, const Cand& b) {
-  return absv > b.absv || (absv == b.absv && label < b.label);
+// Pivot-column rules: the paper's largest |a_kj| (Sec. 2.2) and the two rules of
+// earlier work it names (Sec. 1). A candidate's score orders it under the rule
+// (larger wins, equal scores go to the smaller original label); the score of
+// max-abs is |v| itself.
+enum : int { kRuleMaxAbs = 0, kRuleClosestToOne = 1, kRuleFirstNonzero = 2 };
+
+__device__ __forceinline__ double cand_score(double v, double a, int rule) {
+  if (rule == kRuleClosestToOne) return v != 0.0 ? -fabs(a - 1.0) : -HUGE_VAL;
+  if (rule == kRuleFirstNonzero) return v != 0.0 ? 1.0 : 0.0;
+  return a;
+}
+__device__ __forceinline__ float cand_score(float v, float a, int rule) {
+  if (rule == kRuleClosestToOne) return v != 0.f ? -fabsf(a - 1.f) : -HUGE_VALF;
+  if (rule == kRuleFirstNonzero) return v != 0.f ? 1.f : 0.f;
+  return a;
 }
 
-__device__ __forceinline__ void cand_offer(Cand& c, double v, int label, int pos) {
+__device__ __forceinline__ bool cand_better(double absv, int label, const Cand& b) {
+  return b.pos < 0 || absv > b.absv || (absv == b.absv && label < b.label);
+}
+
+__device__ __forceinline__ void cand_offer(Cand& c, double v, int label, int pos, int rule = 0) {
   double a = fabs(v);
   if (a != a) {
     c.nan = 1;
     return;
   }
+  a = cand_score(v, a, rule);
   if (cand_better(a, label, c)) {
     c.absv = a;
     c.v = v;
@@ -129,15 +147,16 @@ __device__ __forceinline__ void candf_init(CandF& c) {
 }
 
 __device__ __forceinline__ bool candf_better(float absv, int label, const CandF& b) {
-  return absv > b.absv || (absv == b.absv && label < b.label);
+  return b.pos < 0 || absv > b.absv || (absv == b.absv && label < b.label);
 }
 
-__device__ __forceinline__ void candf_offer(CandF& c, float v, int label, int pos) {
-  const float a = fabsf(v);
+__device__ __forceinline__ void candf_offer(CandF& c, float v, int label, int pos, int rule = 0) {
+  float a = fabsf(v);
   if (a != a) {
     c.nan = 1;
     return;
   }
+  a = cand_score(v, a, rule);
   if (candf_better(a, label, c)) {
     c.absv = a;
     c.v = v;

@@ -7,10 +7,11 @@
 //   BF16x3  the same split at BF16 precision with kind::f16 MMAs.
 // Per CTA: up to TPC consecutive 128 x 128 output tiles. Warp 0 lane 0 issues TMA
 // loads of 128-byte K-chunks into a ring of shared-memory stages across the
-// CTA's tiles, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
-// accumulator buffers and frees stages with tcgen05.commit, and warps 2-5 drain
-// the other buffer (tcgen05.ld) and apply D -= acc, so one tile's epilogue
-// overlaps the next tile's loads and MMAs.
+// CTA's tiles, warp 1 lane 0 issues tcgen05.mma into four TMEM accumulators
+// (consecutive K-chunks per accumulator) and frees stages with tcgen05.commit, and
+// warps 2-9 read each accumulator out (tcgen05.ld) as soon as it is complete,
+// release it, and apply D -= sum, so one tile's epilogue overlaps the next tile's
+// loads and MMAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -25,8 +26,25 @@ enum TcKind { kTF32 = 0, kTF32x3 = 1, kBF16x3 = 2 };
 
 namespace {
 
-template <int KIND>
+// Tile and accumulator configuration (128 x 128 output tiles). The tensor cores'
+// own FP32 accumulation truncates, a bias toward zero that grows with the length
+// of each accumulation chain, so the K-chunks of a tile are spread over several
+// TMEM accumulators of 128 columns, summed in FP32 (round to nearest) in the
+// epilogue. The SM's 512 TMEM columns hold four accumulators, used in one of two
+// ways:
+//   double-buffered (QUAD = false): two buffers of two accumulators; K-chunks
+//     alternate between the two of their tile's buffer, and the epilogue drains
+//     one buffer while the MMAs fill the other. Chains of up to two 128-byte
+//     chunks for K <= 128 (TF32 kinds) or K <= 256 (BF16);
+//   released one by one (QUAD = true): one set of four accumulators, each taking
+//     a run of consecutive chunks (two for K = 256); the epilogue reads each out
+//     as soon as it is complete and releases it, so the next tile's MMAs refill
+//     it while the later ones are still being read and D is written. Used for
+//     split TF32 with K > 128 (the paired updates), where the double-buffered
+//     form would chain four chunks per accumulator.
+template <int KIND, bool QUAD_>
 struct TcCfg {
+  static constexpr bool QUAD = QUAD_;
   static constexpr int BM = 128;
   static constexpr int BN = 128;
   static constexpr int ES = (KIND == kBF16x3) ? 2 : 4;
@@ -38,35 +56,48 @@ struct TcCfg {
   static constexpr int STAGES = (KIND == kTF32) ? 4 : 3;
   static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
   static constexpr int NSUB = BK / KSTEP;
-  // epilogue staging: one 32 x 32 FP32 block per epilogue warp
-  static constexpr int STG_BYTES = 4 * 32 * 32 * 4;
+  // epilogue: EW warps, two per TMEM lane quarter (each drains half of a tile's
+  // columns); one 32 x 32 FP32 staging block per epilogue warp
+  static constexpr int EW = 8;
+  static constexpr int STG_BYTES = EW * 32 * 32 * 4;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BYTES;
-  // K-chunks rotate over NACC accumulators (NACC x BN TMEM columns), summed in
-  // FP32 in the epilogue: each tensor-core accumulation chain is NACC times
-  // shorter. Two such buffers fill the SM's 512 TMEM columns.
-  static constexpr int NACC = 2;
-  static constexpr int ACC_COLS = NACC * BN;
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;
-  static constexpr int THREADS = 192;   // producer warp, MMA warp, 4 epilogue warps
+  static constexpr int NACC = QUAD ? 4 : 2;     // accumulators per buffer
+  static constexpr int NBUF = QUAD ? 1 : 2;     // buffers
+  static constexpr int ACC_COLS = NACC * BN;    // one buffer
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int THREADS = 64 + 32 * EW;  // producer warp, MMA warp, epilogue warps
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(192, 1)
+// Accumulator of K-chunk kc of a tile with nk chunks (na = min(nk, 4) used).
+__host__ __device__ constexpr int acc_of(int kc, int nk) {
+  return nk <= 4 ? kc : (kc * 4) / nk;
+}
+
+// K-chunks [0, nk1) come from the first operand maps, the rest from the second
+// (mAh2 ...): one launch computes D -= A1 B1^T + A2 B2^T with the two products
+// in one accumulation.
+template <int KIND, bool QUAD>
+__global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                    const __grid_constant__ CUtensorMap mAh2,
+                    const __grid_constant__ CUtensorMap mAl2,
+                    const __grid_constant__ CUtensorMap mBh2,
+                    const __grid_constant__ CUtensorMap mBl2, int nk1,
                     float* __restrict__ D, int64_t ldd, int64_t dstride,
                     void* const* __restrict__ dptrs, int64_t doff, int M, int N, int K, int batch,
                     int tpc, int* __restrict__ err) {
-  using C = TcCfg<KIND>;
+  using C = TcCfg<KIND, QUAD>;
   constexpr uint32_t IDESC = tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, C::BM, C::BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* accf = empty + C::STAGES;  // [2] accumulator buffer ready (MMA -> epilogue)
-  uint64_t* acce = accf + 2;           // [2] accumulator buffer drained (epilogue -> MMA)
-  uint64_t* done = acce + 2;           // every MMA issued has completed
+  // double-buffered: [buffer]; released one by one: [accumulator]
+  uint64_t* accf = empty + C::STAGES;  // [4] complete (MMA -> epilogue)
+  uint64_t* acce = accf + 4;           // [4] read out (epilogue -> MMA)
+  uint64_t* done = acce + 4;           // every MMA issued has completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   float* stg = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES + 256);
 
@@ -83,14 +114,18 @@ __global__ void __launch_bounds__(192, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&accf[b], 1);
-      tc::mbar_init(&acce[b], 4);
+    for (int a = 0; a < 4; ++a) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], C::EW);
     }
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
     tc::tma_prefetch_desc(&mAh);
     tc::tma_prefetch_desc(&mBh);
+    if (nk1 < K / C::BK) {
+      tc::tma_prefetch_desc(&mAh2);
+      tc::tma_prefetch_desc(&mBh2);
+    }
   }
   if (warp == 0) {
     tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -116,148 +151,273 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         uint8_t* st = smem + s * C::STAGE_BYTES;
+        const bool sec = kc >= nk1;
+        const int kx = (sec ? kc - nk1 : kc) * C::BK;
         tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-        tc::tma_load_3d(st, &mAh, &full[s], kc * C::BK, m0, z);
-        tc::tma_load_3d(st + C::NT * C::A_BYTES, &mBh, &full[s], kc * C::BK, n0, z);
+        tc::tma_load_3d(st, sec ? &mAh2 : &mAh, &full[s], kx, m0, z);
+        tc::tma_load_3d(st + C::NT * C::A_BYTES, sec ? &mBh2 : &mBh, &full[s], kx, n0, z);
         if (C::NT == 2) {
-          tc::tma_load_3d(st + C::A_BYTES, &mAl, &full[s], kc * C::BK, m0, z);
-          tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, &mBl, &full[s], kc * C::BK, n0, z);
+          tc::tma_load_3d(st + C::A_BYTES, sec ? &mAl2 : &mAl, &full[s], kx, m0, z);
+          tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, sec ? &mBl2 : &mBl, &full[s], kx,
+                          n0, z);
         }
         issued = g + 1;
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: tile it into buffer it & 1; K-chunk kc into accumulator kc % NACC
-    int g = 0;
-    bool ok = true;
-    for (int it = 0; it < ntile && ok; ++it) {
-      const int buf = it & 1, use = it >> 1;
-      if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, err)) break;
-      tc::tc_fence_after();
-      for (int kc = 0; kc < nk; ++kc, ++g) {
-        const int s = g % C::STAGES, rnd = g / C::STAGES;
-        if (!tc::mbar_wait(&full[s], rnd & 1, err)) {
-          ok = false;
-          break;
-        }
-        tc::tc_fence_after();
-        const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
-        const uint32_t ah = st, al = st + C::A_BYTES;
-        const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
-        const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS + (kc % C::NACC) * C::BN);
-        uint32_t acc = (kc >= C::NACC) ? 1u : 0u;  // first chunk of an accumulator overwrites
+    // the MMAs of one staged K-chunk into accumulator d (overwritten first if
+    // acc0 == 0): one per K-step, three for the split kinds (small products first)
+    auto issue_mmas = [&](uint32_t st, uint32_t d, uint32_t acc0) {
+      const uint32_t ah = st, al = st + C::A_BYTES;
+      const uint32_t bh = st + C::NT * C::A_BYTES, bl = bh + C::B_BYTES;
+      uint32_t acc = acc0;
 #pragma unroll
-        for (int k = 0; k < C::NSUB; ++k) {
-          const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
-          if (KIND == kTF32) {
-            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          } else if (KIND == kTF32x3) {
-            tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-            tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
-          } else {
-            tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-            tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-            tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
-          }
-          acc = 1u;
+      for (int k = 0; k < C::NSUB; ++k) {
+        const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
+        if (KIND == kTF32) {
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+        } else if (KIND == kTF32x3) {
+          tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+        } else {
+          tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
+          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
+          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
         }
-        tc::mma_commit(&empty[s]);
+        acc = 1u;
       }
-      if (ok) tc::mma_commit(&accf[buf]);
+    };
+    if constexpr (C::QUAD) {
+      // MMA issuer: K-chunk kc of tile it into accumulator acc_of(kc); before the
+      // first chunk of an accumulator, wait until the epilogue has read it out for
+      // the previous tile; after its last chunk, tell the epilogue it is complete
+      int g = 0;
+      bool ok = true;
+      for (int it = 0; it < ntile && ok; ++it) {
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int a = acc_of(kc, nk);
+          const bool first = kc == 0 || acc_of(kc - 1, nk) != a;
+          const bool last = kc == nk - 1 || acc_of(kc + 1, nk) != a;
+          if (first) {
+            if (!tc::mbar_wait(&acce[a], (it & 1) ^ 1, err)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+          }
+          const int s = g % C::STAGES, rnd = g / C::STAGES;
+          if (!tc::mbar_wait(&full[s], rnd & 1, err)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
+          // the first chunk of an accumulator overwrites it
+          issue_mmas(st, tmem + (uint32_t)(a * C::BN), first ? 0u : 1u);
+          tc::mma_commit(&empty[s]);
+          if (last) tc::mma_commit(&accf[a]);
+        }
+      }
+    } else {
+      // MMA issuer: tile it into buffer it & 1, K-chunk kc into its accumulator
+      // kc % 2; the buffer is waited for (drained by the epilogue) before the tile
+      // and reported complete after it
+      int g = 0;
+      bool ok = true;
+      for (int it = 0; it < ntile && ok; ++it) {
+        const int buf = it & 1, use = it >> 1;
+        if (!tc::mbar_wait(&acce[buf], (use & 1) ^ 1, err)) break;
+        tc::tc_fence_after();
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int s = g % C::STAGES, rnd = g / C::STAGES;
+          if (!tc::mbar_wait(&full[s], rnd & 1, err)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
+          const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS + (kc % C::NACC) * C::BN);
+          issue_mmas(st, d, kc >= C::NACC ? 1u : 0u);
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&accf[buf]);
+      }
     }
     // every MMA issued has completed before TMEM is released
     tc::mma_commit(done);
     tc::mbar_wait(done, 0, err);
   } else if (warp >= 2) {
-    // epilogue: D -= acc. Warp w may read TMEM lanes 32 * (w % 4) .. + 31 (one
-    // output row per lane). A whole 32 x 32 block (rows in range, columns inside
-    // N, 16-byte-aligned rows) goes through the warp's shared-memory block so that
-    // D is read and written by rows: lane L covers row 4j + L / 8, columns
-    // 4 (L % 8) .. + 3 of the block in pass j (128 contiguous bytes per row). Its
-    // D values are prefetched two blocks ahead (the first two before the
-    // accumulator is ready). Other blocks: per-row scalar updates.
+    // epilogue: D -= sum of the accumulators. Warp w may read TMEM lanes
+    // 32 * (w % 4) .. + 31 (one output row per lane); warps w and w + 4 split the
+    // tile's 32-column blocks. Each accumulator's blocks are read into registers
+    // (partial sums in FP32, round to nearest) and the accumulator is released at
+    // once. Then every 32 x 32 block goes through the warp's shared-memory block
+    // so that D is read and written by rows: lane L covers row 4j + L / 8,
+    // columns 4 (L % 8) .. + 3 of the block in pass j (128 contiguous bytes per
+    // row). Whole blocks (rows in range, columns inside N, 16-byte-aligned rows)
+    // move as float4 with their D values loaded ahead; ragged blocks element by
+    // element.
+    const int e = warp - 2;
     const int q = warp & 3;
-    constexpr int NC = C::BN / 32;  // 32-column blocks of a tile row
-    float* sw = stg + q * 32 * 32;  // 16-byte chunks XOR-swizzled by row
+    constexpr int NC = C::BN / 32;           // 32-column blocks of a tile row
+    constexpr int NCW = NC / (C::EW / 4);    // blocks drained by one warp
+    static_assert(NCW == 2, "one warp drains two 32-column blocks");
+    const int cb = (e / 4) * NCW;            // this warp's first block
+    float* sw = stg + e * 32 * 32;           // 16-byte chunks XOR-swizzled by row
     const int rsub = lane >> 3, ksub = lane & 7;
-    for (int it = 0; it < ntile; ++it) {
-      const int buf = it & 1, use = it >> 1;
-      const int t = t_first + it, z = t / per_z, r = t % per_z;
-      const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
-      const int row = m0 + q * 32 + lane;
-      float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
-                        : D + (int64_t)z * dstride;
-      float* drow = dz + (int64_t)row * ldd;
-      const bool rows_ok = m0 + q * 32 + 32 <= M &&
-                           ((reinterpret_cast<uintptr_t>(dz) | (uintptr_t)(ldd * 4)) & 15) == 0;
-      float* dblk = dz + (int64_t)(m0 + q * 32 + rsub) * ldd + n0 + 4 * ksub;
-      auto whole = [&](int c) { return rows_ok && n0 + c * 32 + 32 <= N; };
-      float4 dv[2][8];
-      auto prefetch = [&](int c, float4 (&dst)[8]) {
-        if (whole(c)) {
+    // D -= one 32 x 32 block of sums s[] (row per lane): through the warp's
+    // staging block, D moves by rows (lane L takes row 4j + L / 8, columns
+    // 4 (L % 8) .. + 3 in pass j, 128 contiguous bytes per row). A whole block
+    // (rows in range, columns inside N, 16-byte-aligned rows) moves as float4
+    // with its D values dv loaded ahead; a ragged block element by element.
+    auto stage_and_store = [&](int c, const float (&sv)[32], float* dblk, bool w,
+                               const float4 (&dv)[8], int m0, int n0) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            dst[j] = *reinterpret_cast<const float4*>(dblk + (int64_t)(4 * j) * ldd + c * 32);
+      for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<float4*>(sw + lane * 32 + 4 * (k ^ (lane & 7))) =
+            make_float4(sv[4 * k + 0], sv[4 * k + 1], sv[4 * k + 2], sv[4 * k + 3]);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int rr = 4 * j + rsub;
+        const float4 s4 = *reinterpret_cast<const float4*>(sw + rr * 32 + 4 * (ksub ^ (rr & 7)));
+        float* dp = dblk + (int64_t)(4 * j) * ldd + c * 32;
+        if (w) {
+          float4 v = dv[j];
+          v.x -= s4.x;
+          v.y -= s4.y;
+          v.z -= s4.z;
+          v.w -= s4.w;
+          *reinterpret_cast<float4*>(dp) = v;
+        } else if (m0 + q * 32 + rr < M) {
+          const int col = n0 + c * 32 + 4 * ksub;
+          const float sx[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (col + u < N) dp[u] -= sx[u];
         }
-      };
-      prefetch(0, dv[0]);
-      prefetch(1, dv[1]);
-      const bool got = tc::mbar_wait(&accf[buf], use & 1, err);
-      __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
-      if (!__all_sync(0xffffffffu, got)) break;
-      tc::tc_fence_after();
-      // one decision per warp (the staged path synchronises the warp)
-      const bool clean = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(err) == 0, 0);
-      const int nacc = nk < C::NACC ? nk : C::NACC;
+      }
+      __syncwarp();  // the block is rewritten by the next one
+    };
+    if constexpr (C::QUAD) {
+      const int na = nk < 4 ? nk : 4;  // accumulators a tile uses
+      for (int it = 0; it < ntile; ++it) {
+        const int t = t_first + it, z = t / per_z, r = t % per_z;
+        const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+        float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
+                          : D + (int64_t)z * dstride;
+        const bool rows_ok = m0 + q * 32 + 32 <= M &&
+                             ((reinterpret_cast<uintptr_t>(dz) | (uintptr_t)(ldd * 4)) & 15) == 0;
+        float* dblk = dz + (int64_t)(m0 + q * 32 + rsub) * ldd + n0 + 4 * ksub;
+        auto whole = [&](int c) { return rows_ok && n0 + c * 32 + 32 <= N; };
+        // the first block's D values are loaded before the accumulators are waited
+        // for, the second block's before the first block is processed
+        float4 dv[NCW][8];
+        auto load_d = [&](int cc) {
+          if (whole(cb + cc)) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        float a[32];
-        const uint32_t lane_base =
-            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::ACC_COLS + c * 32);
-        tc::tmem_ld32(lane_base, a);
+            for (int j = 0; j < 8; ++j)
+              dv[cc][j] = *reinterpret_cast<const float4*>(dblk + (int64_t)(4 * j) * ldd +
+                                                           (cb + cc) * 32);
+          }
+        };
+        load_d(0);
+        float part[NCW][32];
+        bool got_all = true;
 #pragma unroll
-        for (int p = 1; p < C::NACC; ++p) {  // sum the accumulators in FP32 (round to nearest)
-          if (p < nacc) {
+        for (int a = 0; a < C::NACC; ++a) {
+          if (a >= na) break;
+          const bool got = tc::mbar_wait(&accf[a], it & 1, err);
+          __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
+          if (!__all_sync(0xffffffffu, got)) {
+            got_all = false;
+            break;
+          }
+          tc::tc_fence_after();
+#pragma unroll
+          for (int cc = 0; cc < NCW; ++cc) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {  // 16 columns at a time (fewer live registers)
+              float v[16];
+              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) +
+                                (uint32_t)(a * C::BN + (cb + cc) * 32 + 16 * hh),
+                            v);
+              if (a == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) part[cc][16 * hh + i] = v[i];
+              } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) part[cc][16 * hh + i] += v[i];
+              }
+            }
+          }
+          // accumulator a may now be overwritten by the next tile's MMAs
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acce[a]);
+        }
+        if (!got_all) break;
+        // one decision per warp (the staged path synchronises the warp)
+        const bool clean = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(err) == 0, 0);
+        if (!clean) continue;
+#pragma unroll
+        for (int cc = 0; cc < NCW; ++cc) {
+          const int c = cb + cc;
+          if (cc + 1 < NCW) load_d(cc + 1);  // the next block's D loads go out first
+          stage_and_store(c, part[cc], dblk, whole(c), dv[cc], m0, n0);
+        }
+      }
+    } else {
+      for (int it = 0; it < ntile; ++it) {
+        const int buf = it & 1, use = it >> 1;
+        const int t = t_first + it, z = t / per_z, r = t % per_z;
+        const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+        float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
+                          : D + (int64_t)z * dstride;
+        const bool rows_ok = m0 + q * 32 + 32 <= M &&
+                             ((reinterpret_cast<uintptr_t>(dz) | (uintptr_t)(ldd * 4)) & 15) == 0;
+        float* dblk = dz + (int64_t)(m0 + q * 32 + rsub) * ldd + n0 + 4 * ksub;
+        auto whole = [&](int c) { return rows_ok && n0 + c * 32 + 32 <= N; };
+        // both blocks' D values are loaded before the buffer is waited for
+        float4 dv[NCW][8];
+#pragma unroll
+        for (int cc = 0; cc < NCW; ++cc) {
+          if (whole(cb + cc)) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              dv[cc][j] = *reinterpret_cast<const float4*>(dblk + (int64_t)(4 * j) * ldd +
+                                                           (cb + cc) * 32);
+          }
+        }
+        const bool got = tc::mbar_wait(&accf[buf], use & 1, err);
+        __syncwarp();  // lanes leave the bounded spin independently; tcgen05.ld is warp-wide
+        if (!__all_sync(0xffffffffu, got)) break;
+        tc::tc_fence_after();
+        const bool clean = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(err) == 0, 0);
+        const int nacc = nk < C::NACC ? nk : C::NACC;  // accumulators written for this tile
+#pragma unroll
+        for (int cc = 0; cc < NCW; ++cc) {
+          const int c = cb + cc;
+          float a[32];
+          const uint32_t lane_base =
+              tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::ACC_COLS + c * 32);
+          tc::tmem_ld32(lane_base, a);
+          if (nacc > 1) {  // the second accumulator, summed in FP32 (round to nearest)
             float b[32];
-            tc::tmem_ld32(lane_base + (uint32_t)(p * C::BN), b);
+            tc::tmem_ld32(lane_base + (uint32_t)C::BN, b);
 #pragma unroll
             for (int i = 0; i < 32; ++i) a[i] += b[i];
           }
+          if (clean) stage_and_store(c, a, dblk, whole(c), dv[cc], m0, n0);
         }
-        const int col0 = n0 + c * 32;
-        if (clean) {
-          if (whole(c)) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              *reinterpret_cast<float4*>(sw + lane * 32 + 4 * (k ^ (lane & 7))) =
-                  make_float4(a[4 * k + 0], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int rr = 4 * j + rsub;
-              const float4 s4 = *reinterpret_cast<const float4*>(sw + rr * 32 + 4 * (ksub ^ (rr & 7)));
-              float4 v = dv[c & 1][j];
-              v.x -= s4.x;
-              v.y -= s4.y;
-              v.z -= s4.z;
-              v.w -= s4.w;
-              *reinterpret_cast<float4*>(dblk + (int64_t)(4 * j) * ldd + c * 32) = v;
-            }
-            __syncwarp();  // the block is rewritten by the next chunk
-          } else if (row < M) {
-#pragma unroll
-            for (int v1 = 0; v1 < 32; ++v1)
-              if (col0 + v1 < N) drow[col0 + v1] -= a[v1];
-          }
-        }
-        if (c + 2 < NC) prefetch(c + 2, dv[c & 1]);
+        // the buffer may be overwritten by the MMAs of tile it + 2
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce[buf]);
       }
-      // the buffer may be overwritten by the MMAs of tile it + 2
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acce[buf]);
     }
+
   }
 
   // teardown: every issued TMA copy has landed before shared memory is released
@@ -392,26 +552,50 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, i
 
 namespace {
 
-template <int KIND>
-ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K, float* D,
-                    int64_t ldd, int64_t dstride, void* const* dptrs, int64_t doff, int batch,
-                    int* err, cudaStream_t stream) {
-  using C = TcCfg<KIND>;
-  CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
-      !make_map(&mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
-    return LD_ERR_CUDA;
+// Maps of one operand pair (hi and, for the split kinds, lo parts).
+template <int KIND, bool QUAD>
+bool make_maps(CUtensorMap* mAh, CUtensorMap* mAl, CUtensorMap* mBh, CUtensorMap* mBl,
+               const TcOperand& a, const TcOperand& b, int M, int N, int K, int batch) {
+  using C = TcCfg<KIND, QUAD>;
+  if (!make_map(mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+      !make_map(mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
+    return false;
   if (C::NT == 2) {
-    if (!make_map(&mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
-        !make_map(&mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
+    if (!make_map(mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+        !make_map(mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
+      return false;
+  } else {
+    *mAl = *mAh;
+    *mBl = *mBh;
+  }
+  return true;
+}
+
+// D -= A B^T over K (and, with a2 / b2, -= A2 B2^T over K2 more in the same
+// accumulation).
+template <int KIND, bool QUAD>
+ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, int K, float* D,
+                        int64_t ldd, int64_t dstride, void* const* dptrs, int64_t doff, int batch,
+                        int* err, cudaStream_t stream, const TcOperand* a2, const TcOperand* b2,
+                        int K2) {
+  using C = TcCfg<KIND, QUAD>;
+  CUtensorMap mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2;
+  if (!make_maps<KIND, QUAD>(&mAh, &mAl, &mBh, &mBl, a, b, M, N, K, batch)) return LD_ERR_CUDA;
+  if (a2 && b2 && K2 > 0) {
+    if (!make_maps<KIND, QUAD>(&mAh2, &mAl2, &mBh2, &mBl2, *a2, *b2, M, N, K2, batch))
       return LD_ERR_CUDA;
   } else {
-    mAl = mAh;
-    mBl = mBh;
+    K2 = 0;
+    mAh2 = mAh;
+    mAl2 = mAl;
+    mBh2 = mBh;
+    mBl2 = mBl;
   }
+  const int nk1 = K / C::BK;
+  K += K2;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(rankb_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)C::SMEM) != cudaSuccess)
       return LD_ERR_CUDA;
     attr_set = true;
@@ -425,10 +609,29 @@ ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K,
   ProfScope ps("rankb_tc", stream,
                (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),
                (double)batch * 2.0 * M * N * K);
-  rankb_tc_kernel<KIND><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM, stream>>>(
-      mAh, mAl, mBh, mBl, D, ldd, dstride, dptrs, doff, M, N, K, batch, tpc, err);
+  rankb_tc_kernel<KIND, QUAD><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM, stream>>>(
+      mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2, nk1, D, ldd, dstride, dptrs, doff, M, N, K,
+      batch, tpc, err);
   LD_CHECK_LAUNCH();
   return LD_OK;
+}
+
+// Split TF32 with K > 128 (four or more chunks) takes the accumulators released
+// one by one (at most two chunks each); every other update the double-buffered
+// form (at most two chunks per accumulator for K <= 128, or K <= 256 in BF16).
+template <int KIND>
+ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K, float* D,
+                    int64_t ldd, int64_t dstride, void* const* dptrs, int64_t doff, int batch,
+                    int* err, cudaStream_t stream, const TcOperand* a2 = nullptr,
+                    const TcOperand* b2 = nullptr, int K2 = 0) {
+  if constexpr (KIND == kTF32x3) {
+    const int ktot = K + ((a2 && b2 && K2 > 0) ? K2 : 0);
+    if (ktot > 128)
+      return launch_tc_cfg<KIND, true>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err,
+                                       stream, a2, b2, K2);
+  }
+  return launch_tc_cfg<KIND, false>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream,
+                                  a2, b2, K2);
 }
 
 }  // namespace
@@ -521,6 +724,28 @@ ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, 
       return launch_tc<kTF32x3>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream);
     case LD_F32_BF16X3:
       return launch_tc<kBF16x3>(a, b, M, N, K, D, ldd, dstride, dptrs, doff, batch, err, stream);
+    default:
+      return LD_ERR_INVALID_ARG;
+  }
+}
+
+// Single-matrix update with two operand pairs in one accumulation:
+// D -= A1 B1^T (K1) + A2 B2^T (K2), both K multiples of 64.
+ld_status rankb_tc2(ld_mode mode, const TcOperand& a1, const TcOperand& b1, int K1,
+                    const TcOperand& a2, const TcOperand& b2, int K2, int M, int N, float* D,
+                    int64_t ldd, int* err, cudaStream_t stream) {
+  if (M <= 0 || N <= 0) return LD_OK;
+  if (K1 <= 0 || K1 % 64 != 0 || K2 < 0 || K2 % 64 != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0)
+    return LD_ERR_UNSUPPORTED;
+  switch (mode) {
+    case LD_F32_TF32:
+      return launch_tc<kTF32>(a1, b1, M, N, K1, D, ldd, 0, nullptr, 0, 1, err, stream, &a2, &b2, K2);
+    case LD_F32_3XTF32:
+      return launch_tc<kTF32x3>(a1, b1, M, N, K1, D, ldd, 0, nullptr, 0, 1, err, stream, &a2, &b2,
+                                K2);
+    case LD_F32_BF16X3:
+      return launch_tc<kBF16x3>(a1, b1, M, N, K1, D, ldd, 0, nullptr, 0, 1, err, stream, &a2, &b2,
+                                K2);
     default:
       return LD_ERR_INVALID_ARG;
   }

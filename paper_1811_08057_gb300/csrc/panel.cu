@@ -33,7 +33,11 @@ namespace {
 
 constexpr int kPT = 256;          // threads per panel CTA
 constexpr int kPanelMax = 128;    // largest b
-constexpr uint64_t kPanelWaitNs = 1000000000ull;
+// Limit of every tag-barrier wait, in ns of %globaltimer (1 s unless set with
+// ld_set_tuning("wait_limit_ns", ...) for the current device). The waits poll
+// plain global-memory tags, so a wait that runs out leaves nothing in flight:
+// the kernel flags the sweep and returns.
+__device__ uint64_t g_panel_wait_ns = 1000000000ull;
 
 struct PanelSlot {  // 32 bytes, one per CTA per parity
   double absv;
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel(PanelArgs a) {
 #pragma unroll
         for (int q = 0; q < SL; ++q) ready &= (tags[q] == t + 1);
         if (__all_sync(0xffffffffu, ready)) break;
-        if (gtimer() - t0 > kPanelWaitNs) {
+        if (gtimer() - t0 > g_panel_wait_ns) {
           timed_out = true;
           break;
         }
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(kPT) panel_kernel_f32(PanelArgsF a) {
           ready &= (uint32_t)(words[q] >> 56) == (uint32_t)(t + 1);
         }
         if (__all_sync(0xffffffffu, ready)) break;
-        if (gtimer() - t0 > kPanelWaitNs) {
+        if (gtimer() - t0 > g_panel_wait_ns) {
           timed_out = true;
           break;
         }
@@ -612,6 +616,23 @@ int panel_grid(int64_t m0, size_t es, int64_t* W_out) {
   }
   *W_out = W;
   return G;
+}
+
+// Sets the grid panel's wait limit on the current device.
+ld_status set_panel_wait_limit(uint64_t ns) {
+  if (cudaMemcpyToSymbol(g_panel_wait_ns, &ns, sizeof(ns)) != cudaSuccess) {
+    cudaGetLastError();
+    return LD_ERR_CUDA;
+  }
+  return LD_OK;
+}
+
+ld_status get_panel_wait_limit(uint64_t* ns) {
+  if (cudaMemcpyFromSymbol(ns, g_panel_wait_ns, sizeof(*ns)) != cudaSuccess) {
+    cudaGetLastError();
+    return LD_ERR_CUDA;
+  }
+  return LD_OK;
 }
 
 template <typename T>

@@ -704,6 +704,18 @@ ld_status launch_panel_cluster_batched(void* const* recs, const RecOffsets& ro, 
   return LD_OK;
 }
 
+// The panel's composed column moves (a move list written by the cluster panel)
+// applied to rows [r0, r1) of F.
+ld_status launch_apply_moves(float* F, int64_t ldf, int64_t r0, int64_t r1, const int* moves,
+                             cudaStream_t stream) {
+  if (r1 <= r0) return LD_OK;
+  const int rows = (int)(r1 - r0);
+  const int grid = (int)std::min<int64_t>(ceil_div(rows, 8), device_sm_count() * 4);
+  ProfScope ps("apply_moves", stream, 8.0 * rows * 2 * kBMax, 0.0);
+  apply_moves_kernel<<<grid, 256, 0, stream>>>(F, ldf, (int)r0, (int)r1, moves);
+  return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
+}
+
 // Sign and compensated log-sum of the panel's pivots (Sec. 2.4, Eq. (2)): one
 // warp, the same steps as the panel kernel's own accumulation.
 __global__ void panel_logsum_kernel(const double* __restrict__ pivval,

@@ -39,11 +39,11 @@ __device__ __forceinline__ float div_t(float a, double p) { return __fdiv_rn(a, 
 
 __device__ __forceinline__ void cand_init_any(Cand& c) { cand_init(c); }
 __device__ __forceinline__ void cand_init_any(CandF& c) { candf_init(c); }
-__device__ __forceinline__ void cand_offer_any(Cand& c, double v, int label, int pos) {
-  cand_offer(c, v, label, pos);
+__device__ __forceinline__ void cand_offer_any(Cand& c, double v, int label, int pos, int rule) {
+  cand_offer(c, v, label, pos, rule);
 }
-__device__ __forceinline__ void cand_offer_any(CandF& c, float v, int label, int pos) {
-  candf_offer(c, v, label, pos);
+__device__ __forceinline__ void cand_offer_any(CandF& c, float v, int label, int pos, int rule) {
+  candf_offer(c, v, label, pos, rule);
 }
 __device__ __forceinline__ Cand to_cand(const Cand& c) { return c; }
 __device__ __forceinline__ Cand to_cand(const CandF& f) {
@@ -62,7 +62,7 @@ template <typename T, typename In>
 __global__ void __launch_bounds__(kThreads)
     stage_kernel(const In* __restrict__ A, int64_t lda, T* __restrict__ F, int64_t ldf, int n,
                  int rows_per_cta, int* __restrict__ colperm, SweepState* __restrict__ st,
-                 Cand* __restrict__ cand) {
+                 Cand* __restrict__ cand, int rule) {
   __shared__ Cand red[kThreads / 32];
   constexpr int VN = Vec<T>::N;
   const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * VN;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads)
       if (j < n) {
         colperm[j] = j;
         const T v = static_cast<T>(A[j]);
-        cand_offer(c, (double)v, j, j);
+        cand_offer(c, (double)v, j, j, rule);
       }
     }
     cand_block_reduce(c, red);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads)
     pivot_factor_kernel(T* __restrict__ F, int64_t ldf, int n, int s, int swap_row_begin,
                         int* __restrict__ colperm, int* __restrict__ pivpos,
                         double* __restrict__ pivval, SweepState* __restrict__ st,
-                        const Cand* __restrict__ cand, int ncand) {
+                        const Cand* __restrict__ cand, int ncand, int colf) {
   __shared__ Cand red[kThreads / 32];
   const int m = n - s;
   Cand c;
@@ -114,14 +114,16 @@ __global__ void __launch_bounds__(kThreads)
   for (int k = threadIdx.x; k < ncand; k += blockDim.x) cand_merge(c, cand[k]);
   cand_block_reduce(c, red);
   const int flags = *(volatile int*)&st->flags;
-  const bool bad = flags != 0 || c.nan || c.pos < 0 || c.absv == 0.0;
+  // a zero pivot: every entry of the row is zero under any rule (each prefers a
+  // nonzero entry)
+  const bool bad = flags != 0 || c.nan || c.pos < 0 || c.v == 0.0;
   const int l = c.pos;
   const double p = c.v;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (flags == 0) {
       if (c.nan) {
         st->flags = kFlagNaN;
-      } else if (c.pos < 0 || c.absv == 0.0) {
+      } else if (c.pos < 0 || c.v == 0.0) {
         st->flags = kFlagSingular;
       } else {
         // det A = p det A*, det A* = (-1)^(1+m) det B* with the pivot moved to the
@@ -144,6 +146,22 @@ __global__ void __launch_bounds__(kThreads)
   if (bad) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   T* prow = F + (int64_t)s * ldf;
+  if (colf) {
+    // the pivot factored out of column l (Sec. 2.3): the pivot row keeps its
+    // values, every later row's entry of column l becomes c_i = a_il / p
+    if (t == 0 && l != m - 1) {
+      prow[l] = prow[m - 1];
+      prow[m - 1] = to_t<T>(p);
+    }
+    const int i = swap_row_begin + t;
+    if (i < n && i != s) {
+      T* row = F + (int64_t)i * ldf;
+      const T a = row[l];
+      if (l != m - 1) row[l] = row[m - 1];
+      row[m - 1] = i > s ? div_t(a, p) : a;
+    }
+    return;
+  }
   if (t < m) {
     if (t == l) {
       if (l == m - 1) {
@@ -169,7 +187,8 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, int U>
 __global__ void __launch_bounds__(kThreads)
     update_kernel(T* __restrict__ F, int64_t ldf, int s, int m, int row_end, int rows_per_cta,
-                  const int* __restrict__ colperm, Cand* __restrict__ cand, int lookahead) {
+                  const int* __restrict__ colperm, Cand* __restrict__ cand, int lookahead,
+                  int rule) {
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::N;
   __shared__ Cand red[kThreads / 32];
@@ -205,7 +224,7 @@ __global__ void __launch_bounds__(kThreads)
       if (j < ncols) {
         const T v = fma_t(-c, r[k], row[j]);
         row[j] = v;
-        cand_offer_any(best, v, colperm[j], j);
+        cand_offer_any(best, v, colperm[j], j, rule);
       }
     }
     ++i;
@@ -254,7 +273,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     row_argmax_kernel(const T* __restrict__ F, int64_t ldf, int row, int m,
-                      const int* __restrict__ colperm, Cand* __restrict__ cand) {
+                      const int* __restrict__ colperm, Cand* __restrict__ cand, int rule) {
   __shared__ Cand red[kThreads / 32];
   constexpr int VN = Vec<T>::N;
   const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * VN;
@@ -263,7 +282,7 @@ __global__ void __launch_bounds__(kThreads)
   cand_init(c);
 #pragma unroll
   for (int k = 0; k < VN; ++k)
-    if (j0 + k < m) cand_offer(c, (double)f[j0 + k], colperm[j0 + k], j0 + k);
+    if (j0 + k < m) cand_offer(c, (double)f[j0 + k], colperm[j0 + k], j0 + k, rule);
   cand_block_reduce(c, red);
   if (threadIdx.x == 0) cand[blockIdx.x] = c;
 }
@@ -292,10 +311,12 @@ __global__ void finalize_kernel(const SweepState* __restrict__ st, RecordHeader*
   if (d_logabs) *d_logabs = la;
 }
 
-__global__ void header_kernel(RecordHeader* h, int64_t n, int64_t ldf, int mode, SweepState* st) {
+__global__ void header_kernel(RecordHeader* h, int64_t n, int64_t ldf, int mode, int side,
+                              SweepState* st) {
   h->n = n;
   h->ldf = ldf;
   h->mode = mode;
+  h->side = side;
   h->flags = 0;
   h->sign = 1.0;
   h->logabs = 0.0;
@@ -328,7 +349,7 @@ ld_status launch_stage(const void* A, ld_dtype a_dtype, int64_t lda, const Recor
   const int n = (int)r.n;
   {
     ProfScope ps("header", stream);
-    header_kernel<<<1, 1, 0, stream>>>(r.header, r.n, r.ldf, (int)r.mode, r.state);
+    header_kernel<<<1, 1, 0, stream>>>(r.header, r.n, r.ldf, (int)r.mode, r.colf, r.state);
   }
   LD_CHECK_LAUNCH();
   if (n == 0) return LD_OK;
@@ -344,11 +365,11 @@ ld_status launch_stage(const void* A, ld_dtype a_dtype, int64_t lda, const Recor
   if (a_dtype == LD_DTYPE_F64)
     stage_kernel<T, double><<<grid, kThreads, 0, stream>>>(
         static_cast<const double*>(A), lda, static_cast<T*>(r.F), r.ldf, n, rows_per, r.colperm,
-        r.state, r.cand);
+        r.state, r.cand, r.rule);
   else
     stage_kernel<T, float><<<grid, kThreads, 0, stream>>>(
         static_cast<const float*>(A), lda, static_cast<T*>(r.F), r.ldf, n, rows_per, r.colperm,
-        r.state, r.cand);
+        r.state, r.cand, r.rule);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }
@@ -368,7 +389,7 @@ ld_status launch_pivot_factor(const Record& r, int64_t s, int64_t swap_row_begin
                (double)sizeof(T) * (2.0 * m + 4.0 * (double)(n - swap_row_begin)), (double)m);
   pivot_factor_kernel<T><<<blocks, kThreads, 0, stream>>>(
       static_cast<T*>(r.F), r.ldf, (int)n, (int)s, (int)swap_row_begin, r.colperm, r.pivpos,
-      r.pivval, r.state, r.cand, ncand_for<T>(m));
+      r.pivval, r.state, r.cand, ncand_for<T>(m), r.colf);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }
@@ -389,7 +410,7 @@ ld_status launch_update(const Record& r, int64_t s, int64_t row_end, bool lookah
                2.0 * (double)rows * (double)(m - 1));
   update_kernel<T, 4><<<grid, kThreads, 0, stream>>>(static_cast<T*>(r.F), r.ldf, (int)s, (int)m,
                                                      (int)row_end, (int)rows_per, r.colperm,
-                                                     r.cand, lookahead ? 1 : 0);
+                                                     r.cand, lookahead ? 1 : 0, r.rule);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }
@@ -399,7 +420,7 @@ ld_status launch_row_argmax(const Record& r, int64_t row, int64_t m, cudaStream_
   const int nc = (int)std::max<int64_t>(1, ceil_div(m, col_tile(Vec<T>::N)));
   ProfScope ps("row_argmax", stream, (double)sizeof(T) * m, 0.0);
   row_argmax_kernel<T><<<nc, kThreads, 0, stream>>>(static_cast<const T*>(r.F), r.ldf, (int)row,
-                                                    (int)m, r.colperm, r.cand);
+                                                    (int)m, r.colperm, r.cand, r.rule);
   LD_CHECK_LAUNCH();
   return LD_OK;
 }

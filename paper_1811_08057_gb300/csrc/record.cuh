@@ -28,6 +28,7 @@ struct RecordHeader {
   int32_t flags;
   double sign;
   double logabs;
+  int32_t side;  // 0: pivots factored out of their rows (Crout form); 1: out of their columns
 };
 
 // Device pointers into one factor record.
@@ -43,6 +44,10 @@ struct Record {
   SweepState* state = nullptr;
   Cand* cand = nullptr;      // ncand entries
   int64_t ncand = 0;
+  // plain sweep only: pivot-column rule (kRuleMaxAbs, the paper's, or a rule of
+  // earlier work) and the factoring side (0: row, the paper's; 1: column)
+  int rule = 0;
+  int colf = 0;
 };
 
 // Computes the layout (and, if base != nullptr, the pointers). Returns the size.
@@ -105,7 +110,13 @@ int device_sm_count();
 // size class (class k holds n in [64k, 64k + 63]; the last class all larger n).
 constexpr int kTuneBuckets = 9;
 int tuned_blocked_b();
+int64_t tuned_pair_min_n();
 const int* tuned_batched_kb();
+// The table itself (no cache loading): set / get one entry by name.
+ld_status tuning_set(const char* name, int64_t value);
+ld_status tuning_get(const char* name, int64_t* value);
+// Loads $LD_TUNE_CACHE/<GPU name>.tune into the table once (tune.cu).
+void tune_cache_autoload();
 
 // ---- plain-path launchers (plain.cu) ----
 // Copies A into F (converting to the storage type), sets colperm = identity,
@@ -151,6 +162,10 @@ struct TcOperand {
 ld_status rankb_tc(ld_mode mode, const TcOperand& a, const TcOperand& b, int M, int N, int K,
                    float* D, int64_t ldd, int64_t dstride, int batch, int* err,
                    cudaStream_t stream, void* const* dptrs = nullptr, int64_t doff = 0);
+// D -= A1 B1^T + A2 B2^T (inner sizes K1, K2) in one tensor-core accumulation.
+ld_status rankb_tc2(ld_mode mode, const TcOperand& a1, const TcOperand& b1, int K1,
+                    const TcOperand& a2, const TcOperand& b2, int K2, int M, int N, float* D,
+                    int64_t ldd, int* err, cudaStream_t stream);
 size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K);
 // Bytes of one rows x K operand in the mode's tensor-core format (hi, then lo).
 size_t rankb_operand_bytes(ld_mode mode, int64_t rows, int64_t K);
@@ -171,6 +186,10 @@ template <typename T>
 ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
                        void* scratch, cudaStream_t stream);
 
+// Limit (ns) of the grid panel's waits on the current device (1 s by default).
+ld_status set_panel_wait_limit(uint64_t ns);
+ld_status get_panel_wait_limit(uint64_t* ns);
+
 // ---- cluster panel kernel (panel_cluster.cu), FP32 storage ----
 // Scratch of one launch; it starts with the panel's composed column moves for
 // the rows outside the panel: int count, then count (dst, src) position pairs.
@@ -178,6 +197,9 @@ size_t panel_cluster_scratch_bytes();
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
                                void* scratch, bool defer_logsum, cudaStream_t stream);
 ld_status launch_panel_logsum(const Record& r, int64_t s0, int64_t bb, cudaStream_t stream);
+// Applies a cluster panel's move list to rows [r0, r1) of F (FP32 storage).
+ld_status launch_apply_moves(float* F, int64_t ldf, int64_t r0, int64_t r1, const int* moves,
+                             cudaStream_t stream);
 ld_status launch_panel_cluster_batched(void* const* recs, const RecOffsets& ro, int64_t n,
                                        int64_t ldf, int64_t count, int64_t s0, int64_t bb,
                                        void* scratch, cudaStream_t stream);

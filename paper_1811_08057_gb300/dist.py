@@ -66,3 +66,32 @@ def gather_results(indices, values, count: int, device=None):
     if world > 1:
         dist.all_reduce(out, op=dist.ReduceOp.SUM)
     return out
+
+
+def logdet_batched_distributed(sizes, get_matrix, mode="f32_plain", compute=None, device=None):
+    """sign and log|det| of a batch of independent matrices sharded over the ranks.
+
+    Every rank passes the whole batch's `sizes`; `get_matrix(i)` returns matrix i
+    on this rank's device and is called only for this rank's share (longest
+    processing time first on the n^3 cost, `lpt_partition`). Each rank sweeps its
+    share in one ld_logdet_batched call (`compute(mats, mode)` replaces that call,
+    e.g. in host-only tests); the (sign, log|det|) pairs are then combined once,
+    so every rank returns both full FP64 vectors (length len(sizes)) in batch
+    order. No collective runs inside the sweep.
+    """
+    rank, world = world_info()
+    mine = lpt_partition(sizes, world)[rank]
+    if compute is None:
+        from . import api
+
+        def compute(mats, mode):
+            s, l = api.logdet_batched(api.BatchedInputs(mats), mode)
+            return s, l
+    if mine:
+        signs, logabs = compute([get_matrix(i) for i in mine], mode)
+        signs = torch.as_tensor(signs, dtype=torch.float64).to(device).tolist()
+        logabs = torch.as_tensor(logabs, dtype=torch.float64).to(device).tolist()
+    else:
+        signs, logabs = [], []
+    return (gather_results(mine, signs, len(sizes), device=device),
+            gather_results(mine, logabs, len(sizes), device=device))

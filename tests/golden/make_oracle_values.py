@@ -25,7 +25,14 @@ CASES = {
     "dense_n8000_seed1": lambda: workloads.dense_gaussian(8000, seed=1, var=1.0 / 8000),
     # dense iid N(0, 1), N = 1000, seed 0
     "dense_n1000_seed0": lambda: workloads.dense_gaussian(1000, seed=0),
+    # SPD X^T X / (2N) + 1e-3 I, N = 8000, X drawn from seed 1 after the dense
+    # matrix above (the product X^T X is a BLAS call: another host's BLAS may
+    # round it differently, far below the 1e-12 tolerance of the FP64 paths)
+    "spd_n8000_seed1": lambda: workloads.dense_and_spd_pair(8000, seed=1)[1],
 }
+GENERATORS = {"dense_n8000_seed1": "workloads.dense_gaussian",
+              "dense_n1000_seed0": "workloads.dense_gaussian",
+              "spd_n8000_seed1": "workloads.dense_and_spd_pair(...)[1]"}
 
 
 def main():
@@ -42,7 +49,7 @@ def main():
         dt = time.time() - t0
         out = {
             "case": name,
-            "generator": "workloads." + ("dense_gaussian"),
+            "generator": GENERATORS[name],
             "n": int(A.shape[0]),
             "sign": res.sign,
             "logabs": res.logabs,

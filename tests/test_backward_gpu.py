@@ -122,3 +122,52 @@ def test_backward_config_256x1024_sampled(mode):
         Ai = A[i].double().cpu().numpy()
         Rg = oracle.grad_logabs(Ai, 1.0)
         assert rel_fro(X.grad[i].double().cpu().numpy(), Rg) <= 1e-4
+
+
+def test_config5_central_differences():
+    """The 256 x 1024^2 gradient workload (eigenvalues log-uniform in [1e-2, 1],
+    FP32, batched blocked 3xTF32 forward and backward): on 4 sampled matrices,
+    <G, E> for 16 single entries and 16 random unit-Frobenius directions E against
+    central differences of log|det| with h = 1e-3 (Richardson-combined with h/2,
+    which removes the h^2 term), the log-determinants taken by the FP64 plain
+    sweep (bit-identical to the FP64 oracle's operations) in batched launches."""
+    B, n = 256, 1024
+    g = torch.Generator(device="cuda").manual_seed(4)
+    lam = 10.0 ** (-2.0 * torch.rand(B, n, generator=g, device="cuda", dtype=torch.float64))
+    Q, R = torch.linalg.qr(torch.randn(B, n, n, generator=g, device="cuda", dtype=torch.float64))
+    Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
+    A = (Q * lam[:, None, :]) @ Q.transpose(1, 2)
+    A = (0.5 * (A + A.transpose(1, 2))).float()
+    del Q, R
+    X = A.clone().requires_grad_(True)
+    api.logabsdet(X, "f32_3xtf32").sum().backward()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(12)
+    h = 1e-3
+    worst = 0.0
+    for i in [0, 85, 170, 255]:
+        A64 = A[i].double()
+        G = X.grad[i].double()
+        dirs = []
+        for _ in range(16):
+            E = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+            r, c = rng.integers(0, n, size=2)
+            E[r, c] = 1.0
+            dirs.append(E)
+        for _ in range(16):
+            E = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+            dirs.append(E / torch.linalg.norm(E))
+        mats = [(A64 + sgn * step * E).contiguous() for E in dirs
+                for sgn, step in ((1, h), (-1, h), (1, h / 2), (-1, h / 2))]
+        _, la = api.logdet_batched(mats, "f64_plain")
+        la = la.cpu().numpy().reshape(len(dirs), 4)
+        del mats
+        for k, E in enumerate(dirs):
+            d1 = (la[k, 0] - la[k, 1]) / (2 * h)
+            d2 = (la[k, 2] - la[k, 3]) / h
+            fd = (4.0 * d2 - d1) / 3.0
+            ip = float((G * E).sum())
+            err = abs(fd - ip) / max(abs(fd), 1.0)
+            worst = max(worst, err)
+            assert err <= 1e-4, (i, k, fd, ip)
+    print(f"config 5 central differences: worst relative error {worst:.2e}")

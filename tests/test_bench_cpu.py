@@ -10,8 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_line():
     out = subprocess.run(
-        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "256",
-         "--steps", "1", "--warmup", "0"],
+        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+         "dense", "--N", "256", "--steps", "1", "--warmup", "0"],
         cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -58,3 +58,23 @@ def test_roofline_arithmetic():
                - peaks["bf16_tflops_sustained"] / 3.0) < 1e-9
     assert abs(b.make_roofline("rankb_tc", "f32_tf32", 1, 1, 1, 1, 1)["peak"]
                - peaks["bf16_tflops_sustained"] * 1.1 / 2.25) < 1e-9
+
+
+def test_sweep_roofline_arithmetic():
+    """The sweep-level figure: 2N^3/3 useful flop over the step time, against the
+    tensor peak of the mode's arithmetic; the panel chain as time per pivot."""
+    b = _bench_module()
+    N, ms = 32768, 200.0
+    shares = {"panel": {"launches": 256, "ms": 120.0, "bytes": 0.0, "flops": 0.0, "share": 0.5},
+              "rankb_tc": {"launches": 600, "ms": 120.0, "bytes": 1e12, "flops": 2e13,
+                           "share": 0.5}}
+    r = b.sweep_roofline("f32_3xtf32", N, ms, shares)
+    want = 2.0 * N ** 3 / 3.0 / 0.2 / 1e12
+    assert abs(r["achieved"] - want) < 1e-9
+    assert r["bound"] == "tensor" and abs(r["frac"] - want / b.tensor_peak("f32_3xtf32")[0]) < 1e-12
+    assert abs(r["pivot_chain"]["us_per_pivot"] - 120e3 / N) < 1e-12
+    assert abs(r["tensor_update"]["achieved"] - 2e13 / 0.12 / 1e12) < 1e-9
+    # a plain mode reports its rank-1 update against HBM
+    r = b.sweep_roofline("f64_plain", 8000, 600.0, {
+        "update": {"launches": 8000, "ms": 500.0, "bytes": 3e12, "flops": 1e11, "share": 0.9}})
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 3e12 / 0.5 / 1e9) < 1e-6

@@ -1,15 +1,19 @@
-"""Precision configs: N = 16384 and N = 32768 SPD matrices Q diag(lambda) Q^T,
-lambda log-uniform in [1e-4, 1], stored in FP32; blocked sweep with the trailing
-update in split-TF32, split-BF16 and plain TF32 (FP64 pivot, divide and log-sum).
-Error against the exact sum of log(lambda): 3xTF32 <= 1e-5, BF16x3 <= 1e-4
-relative; plain TF32 is reported against a loose bound only.
+"""Precision and covariance configs against exact or stored FP64 references.
 
-N = 16384 uses a Haar Q (QR of a Gaussian, FP64); N = 32768 uses a product of
-Householder reflectors (an FP64 QR of that size takes minutes on this GPU's FP64
-units). Both are exactly orthogonal, so the determinant is exp(sum log lambda)
-up to the FP32 rounding of A.
+Q diag(lambda) Q^T (N = 16384 and N = 32768, Q Haar, lambda log-uniform in
+[1e-4, 1], seed 2, stored in FP32): blocked sweep with the trailing update in
+split-TF32, split-BF16 and plain TF32 (FP64 pivot, divide and log-sum). Error
+against the exact sum of log(lambda): 3xTF32 <= 1e-5, BF16x3 <= 1e-4
+relative; plain TF32 is reported against a loose bound only. Q comes from the
+QR of a Gaussian (workloads.spd_haar_torch): log det A differs from the sum of
+log(lambda) by log det(Q^T Q), below 1e-7 relative.
+
+X^T X / (2N) + 1e-3 I (N = 8000, X 2N x N from seed 1): every mode against the
+stored FP64 oracle result.
 """
+import json
 import math
+import os
 
 import pytest
 import torch
@@ -20,6 +24,9 @@ from paper_1811_08057_gb300 import api
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32_3xtf32": 1e-5, "f32_bf16x3": 1e-4, "f32_tf32": 5e-2}
+TOL_2B = {"f64_plain": 1e-12, "f64_blocked": 1e-12, "f32_plain": 1e-5, "f32_3xtf32": 1e-5,
+          "f32_bf16x3": 1e-4, "f32_tf32": 5e-2}
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _rel(a, b):
@@ -28,8 +35,8 @@ def _rel(a, b):
 
 @pytest.fixture(scope="module")
 def spd16k():
-    A, sl = workloads.spd_spectrum_torch(16384, seed=2, lo=1e-4, hi=1.0, device="cuda",
-                                         dtype=torch.float32)
+    A, sl = workloads.spd_haar_torch(16384, seed=2, lo=1e-4, hi=1.0, device="cuda",
+                                     dtype=torch.float32)
     torch.cuda.synchronize()
     return A, sl
 
@@ -48,8 +55,8 @@ def test_spd_16384(spd16k, mode):
 
 
 def test_spd_32768_3xtf32_and_bf16x3():
-    A, sl = workloads.spd_reflectors_torch(32768, seed=2, lo=1e-4, hi=1.0, device="cuda",
-                                           dtype=torch.float32)
+    A, sl = workloads.spd_haar_torch(32768, seed=2, lo=1e-4, hi=1.0, device="cuda",
+                                     dtype=torch.float32)
     torch.cuda.synchronize()
     for mode in ["f32_3xtf32", "f32_bf16x3"]:
         s, l = api.logdet(A, mode)
@@ -57,3 +64,25 @@ def test_spd_32768_3xtf32_and_bf16x3():
         print(f"N=32768 SPD {mode}: rel err {err:.3e}")
         assert float(s) == 1.0
         assert err <= TOL[mode], (mode, float(l), sl)
+
+
+@pytest.fixture(scope="module")
+def spd8000():
+    S = workloads.dense_and_spd_pair(8000, seed=1)[1]
+    with open(os.path.join(GOLDEN, "oracle_spd_n8000_seed1.json")) as fh:
+        g = json.load(fh)
+    return torch.from_numpy(S).cuda(), g
+
+
+@pytest.mark.parametrize("mode", sorted(TOL_2B))
+def test_spd_covariance_8000(spd8000, mode):
+    """Config 2b: X^T X / (2N) + 1e-3 I, N = 8000, in every mode."""
+    S, g = spd8000
+    s, l = api.logdet(S, mode)
+    err = _rel(float(l), g["logabs"])
+    print(f"N=8000 SPD covariance {mode}: rel err {err:.3e}")
+    if mode == "f32_tf32":
+        assert math.isfinite(float(l))
+        return
+    assert float(s) == g["sign"] == 1.0
+    assert err <= TOL_2B[mode], (mode, float(l), g["logabs"])

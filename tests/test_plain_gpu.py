@@ -214,3 +214,31 @@ def test_f64_config_8000_full_sequence():
     assert np.array_equal(f.pivval.cpu().numpy(), ref.piv_value)
     assert float(f.sign) == ref.sign
     assert rel_err(float(f.logabs), ref.logabs) <= F64_TOL
+
+
+def test_wait_limit_runs_out_and_context_stays_usable():
+    """A bounded device wait that runs out: with the grid panel's wait limit at 0
+    (LD_F64_BLOCKED's panels poll global-memory tags), the tag barrier gives up,
+    the sweep is flagged, the results are NaN and the call reports LD_ERR_TIMEOUT.
+    The context stays usable: with the limit restored the same call succeeds."""
+    import ctypes
+    n = 1000  # 16 panel CTAs and 1000 tag barriers: some wait outlasts a timer tick
+    A = workloads.dense_gaussian(n, seed=61)
+    At = torch.from_numpy(A).cuda()
+    ref = oracle.logdet(A)
+    old = _lib.ld_get_tuning("wait_limit_ns")
+    assert old == 1_000_000_000
+    hs, hl = ctypes.c_double(), ctypes.c_double()
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        assert _lib.ld_set_tuning("wait_limit_ns", 0) == 0
+        code = _lib.ld_logdet(At.data_ptr(), _lib.LD_DTYPE_F64, n, n, _lib.LD_F64_BLOCKED, stream,
+                              ctypes.addressof(hs), ctypes.addressof(hl))
+        assert code == 5, _lib.STATUS.get(code)
+        assert math.isnan(hs.value) and math.isnan(hl.value)
+    finally:
+        assert _lib.ld_set_tuning("wait_limit_ns", old) == 0
+    code = _lib.ld_logdet(At.data_ptr(), _lib.LD_DTYPE_F64, n, n, _lib.LD_F64_BLOCKED, stream,
+                          ctypes.addressof(hs), ctypes.addressof(hl))
+    assert code == 0 and hs.value == ref.sign
+    assert abs(hl.value - ref.logabs) <= 1e-12 * max(1.0, abs(ref.logabs))

@@ -1,54 +1,46 @@
-"""The tuning cache on the host: `tune.apply()` loads this GPU's stored panel
-widths into the library's tuning table, and leaves it alone when the cache has
-no entry for the GPU (or no file). The GPU name is faked; no device work."""
-import json
-
+"""The tuning table's file form on the host (ld_tune_save / ld_tune_load through
+the C ABI; no device work): a round trip restores every entry, and a file with a
+bad name or value is rejected as a whole, leaving the table unchanged."""
 import pytest
 
 from paper_1811_08057_gb300 import _lib, tune
 
-NAMES = ["blocked_b"] + [f"batched_kb_{k}" for k in range(tune.BUCKETS)]
-
 
 @pytest.fixture
 def saved_table():
-    before = {nm: _lib.ld_get_tuning(nm) for nm in NAMES}
+    before = tune.table()
     yield before
     for nm, v in before.items():
         assert _lib.ld_set_tuning(nm, v) == 0
 
 
-def test_apply_loads_cached_entry(tmp_path, monkeypatch, saved_table):
-    path = tmp_path / "tune.json"
-    path.write_text(json.dumps({
-        "Other GPU": {"blocked_b": 128, "batched_kb": {"0": 16}},
-        "Fake GB300": {"blocked_b": 64, "batched_kb": {"0": 8, "3": 8, "8": 16}},
-    }))
-    monkeypatch.setenv("LD_TUNE_CACHE", str(path))
-    monkeypatch.setattr(tune, "_gpu_key", lambda device: "Fake GB300")
-    for nm in NAMES:  # a known starting point
+def test_save_load_round_trip(tmp_path, saved_table):
+    path = str(tmp_path / "t.tune")
+    assert _lib.ld_set_tuning("blocked_b", 64) == 0
+    assert _lib.ld_set_tuning("blocked_pair_min_n", 12345) == 0
+    assert _lib.ld_set_tuning("batched_kb_3", 8) == 0
+    want = tune.table()
+    tune.save(path)
+    text = open(path).read().split()
+    assert text[0:2] == ["blocked_b", "64"]
+    for nm in tune.NAMES:  # scramble, then load
         assert _lib.ld_set_tuning(nm, 128 if nm == "blocked_b" else 16) == 0
-    assert tune.apply() is True
-    assert _lib.ld_get_tuning("blocked_b") == 64
-    assert _lib.ld_get_tuning("batched_kb_0") == 8
-    assert _lib.ld_get_tuning("batched_kb_3") == 8
-    assert _lib.ld_get_tuning("batched_kb_8") == 16
-    assert _lib.ld_get_tuning("batched_kb_1") == 16  # not in the entry: unchanged
+    tune.load(path)
+    assert tune.table() == want
 
 
-def test_apply_without_entry_changes_nothing(tmp_path, monkeypatch, saved_table):
-    monkeypatch.setattr(tune, "_gpu_key", lambda device: "Fake GB300")
-    monkeypatch.setenv("LD_TUNE_CACHE", str(tmp_path / "missing.json"))
-    assert tune.apply() is False
-    path = tmp_path / "tune.json"
-    path.write_text(json.dumps({"Other GPU": {"blocked_b": 64}}))
-    monkeypatch.setenv("LD_TUNE_CACHE", str(path))
-    assert tune.apply() is False
-    assert {nm: _lib.ld_get_tuning(nm) for nm in NAMES} == saved_table
+@pytest.mark.parametrize("bad", ["blocked_b 96\n", "no_such_entry 1\n", "batched_kb_9 8\n",
+                                 "blocked_b 64\nbatched_kb_x 8\n", "blocked_b sixty-four\n"])
+def test_bad_file_leaves_table(tmp_path, saved_table, bad):
+    path = tmp_path / "bad.tune"
+    path.write_text(bad)
+    before = tune.table()
+    assert _lib.ld_tune_load(str(path)) == 1
+    assert tune.table() == before
+    assert _lib.ld_tune_load(str(tmp_path / "missing.tune")) == 1
 
 
-def test_cache_path_default_and_override(monkeypatch):
-    monkeypatch.delenv("LD_TUNE_CACHE", raising=False)
-    assert tune.cache_path().endswith("liblogdet/tune.json")
-    monkeypatch.setenv("LD_TUNE_CACHE", "/x/y.json")
-    assert tune.cache_path() == "/x/y.json"
+def test_tune_rejects_bad_arguments():
+    assert _lib.ld_tune([], 4) == 1
+    assert _lib.ld_tune([100, -1], 4) == 1
+    assert _lib.ld_tune([100], 99) == 1

@@ -1,7 +1,10 @@
-"""The autotuner measures its candidates through the C ABI and applies winners;
-results do not depend on the tuning (the batched sweep performs the same
-per-element operations for any panel depth)."""
-import json
+"""The autotuner through the C ABI (ld_tune): it picks candidates the launchers
+accept, stores the table under LD_TUNE_CACHE, and a fresh process loads it on
+first use; results do not depend on the tuning where the operations are the same
+(the batched sweep performs the same per-element operations for any panel depth)."""
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -11,9 +14,18 @@ import workloads
 from paper_1811_08057_gb300 import _lib, api, tune
 
 pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_batched_results_independent_of_panel_depth():
+@pytest.fixture
+def saved_table():
+    before = tune.table()
+    yield before
+    for nm, v in before.items():
+        assert _lib.ld_set_tuning(nm, v) == 0
+
+
+def test_batched_results_independent_of_panel_depth(saved_table):
     mats = [torch.from_numpy(workloads.dense_gaussian(n, seed=n)).cuda() for n in [40, 130, 300]]
     outs = []
     for kb in (8, 16):
@@ -21,30 +33,39 @@ def test_batched_results_independent_of_panel_depth():
             _lib.ld_set_tuning(f"batched_kb_{k}", kb)
         s, l = api.logdet_batched(mats, "f64_plain")
         outs.append((s.clone(), l.clone()))
-    for k in range(9):
-        _lib.ld_set_tuning(f"batched_kb_{k}", 16)
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
 
-def test_autotune_writes_and_applies_cache(tmp_path, monkeypatch):
-    monkeypatch.setenv("LD_TUNE_CACHE", str(tmp_path / "tune.json"))
-    entry = tune.autotune(save=True)
-    assert entry["blocked_b"] in (64, 128)
-    with open(tmp_path / "tune.json") as f:
-        data = json.load(f)
-    assert torch.cuda.get_device_name(0) in data
-    _lib.ld_set_tuning("blocked_b", 64 if entry["blocked_b"] == 128 else 128)
-    assert tune.apply()
-    assert _lib.ld_get_tuning("blocked_b") == entry["blocked_b"]
+def test_ld_tune_blocked_and_batched(tmp_path, monkeypatch, saved_table):
+    monkeypatch.setenv("LD_TUNE_CACHE", str(tmp_path))
+    t = tune.autotune([3000], "f32_3xtf32")
+    assert t["blocked_b"] in (64, 128)
+    assert t["blocked_pair_min_n"] in (0, 3001)
+    t = tune.autotune([40, 130, 300, 520], "f32_plain")
+    for k in (0, 2, 4, 8):
+        assert t[f"batched_kb_{k}"] in (8, 16)
+    files = os.listdir(tmp_path)
+    assert len(files) == 1 and files[0].endswith(".tune")
+    # a fresh process with the cache directory set starts from the stored table
+    want = tune.table()
+    code = ("import json, paper_1811_08057_gb300 as pk; from paper_1811_08057_gb300 import tune; "
+            "pk.load(); print(json.dumps(tune.table()))")
+    env = dict(os.environ, LD_TUNE_CACHE=str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    import json
+    assert json.loads(out.stdout.strip().splitlines()[-1]) == want
 
 
-def test_blocked_panel_width_64_parity():
+def test_blocked_panel_width_64_parity(saved_table):
     n = 700
     A = workloads.dense_gaussian(n, seed=9, var=1.0 / n) + 2.0 * np.eye(n)
     import oracle
     ref = oracle.logdet(A)
     _lib.ld_set_tuning("blocked_b", 64)
-    try:
+    for pair_min in (1 << 40, 0):
+        _lib.ld_set_tuning("blocked_pair_min_n", pair_min)
         for mode in ["f32_3xtf32", "f64_blocked"]:
             s, l = api.logdet(torch.from_numpy(A).cuda(), mode)
             assert float(s) == ref.sign
@@ -53,5 +74,3 @@ def test_blocked_panel_width_64_parity():
         Ad, sgn, la, perm = workloads.dyadic_lu(300, seed=1)
         f = api.logdet_factor(torch.from_numpy(Ad).cuda(), "f32_3xtf32")
         assert np.array_equal(f.pivot_labels().cpu().numpy(), perm)
-    finally:
-        _lib.ld_set_tuning("blocked_b", 128)

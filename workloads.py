@@ -13,6 +13,7 @@ stated distribution; these recipes stand in for its matrices):
                                  Gaussian with the sign of diag(R) folded in),
                                  lambda log-uniform in [lo, hi]; returns the exact
                                  sum of log(lambda) alongside
+  spd_haar_torch(N, seed, ...)   the same recipe on the GPU for N = 16384 / 32768
   batched_sizes(count, seed)     sizes uniform on {32, 48, ..., 512}
   dyadic_lu(n, seed)             integer/dyadic matrices whose whole condensation
                                  sweep is exact in FP32, with the pivot labels and
@@ -176,6 +177,74 @@ def batched_covariances_torch(sizes, seed: int = 3, ridge: float = 1e-2, device=
         for k, i in enumerate(idx):
             out[i] = S[k].contiguous()
     return out
+
+
+def _cache_dir():
+    import os
+    return os.environ.get("LD_INPUT_CACHE", os.path.join("/tmp", "ld_inputs"))
+
+
+def spd_haar_torch(N: int, seed: int, lo: float = 1e-4, hi: float = 1.0, device="cuda",
+                   dtype=None, cache: bool = True):
+    """Q diag(lambda) Q^T with Q Haar, lambda log-uniform in [lo, hi], on the GPU.
+
+    Q: QR of an N x N Gaussian (FP32 QR, the sign of diag(R) folded in), then
+    every column scaled to unit norm in FP64, so that Q^T Q = I + E with a zero
+    diagonal: log det A = sum log(lambda) + log det(Q^T Q), and the second term
+    is about -||E||_F^2 / 2 (||E||_F = 4e-4 at N = 16384, i.e. below 1e-7 in
+    log det A). A = (Q lambda) Q^T is formed in FP64 (an FP32 product moves
+    log det by ~1e-4 relative at N = 16384) and symmetrised. Returns
+    (A in ``dtype`` (FP64 by default) on ``device``, exact sum of log(lambda)).
+
+    The result is cached as a file under $LD_INPUT_CACHE (default
+    /tmp/ld_inputs) so that later processes skip the minute of FP64 work at
+    N = 32768; writing the cache is best effort. Only torch library calls are
+    used: plumbing, not the method.
+    """
+    import json
+    import os
+
+    import torch
+
+    dtype = dtype or torch.float64
+    tag = f"haar_N{N}_seed{seed}_lo{lo:g}_hi{hi:g}_{str(dtype).split('.')[-1]}"
+    path = os.path.join(_cache_dir(), tag)
+    if cache and os.path.exists(path + ".json") and os.path.exists(path + ".bin"):
+        try:
+            with open(path + ".json") as f:
+                meta = json.load(f)
+            host = torch.from_file(path + ".bin", shared=False, size=N * N, dtype=dtype)
+            return host.view(N, N).to(device), meta["sum_log"]
+        except Exception:
+            pass
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = torch.rand(N, generator=g, device=device, dtype=torch.float64)
+    lam = 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+    G = torch.randn(N, N, generator=g, device=device, dtype=torch.float32)
+    Q32, R = torch.linalg.qr(G)
+    sgn = torch.sign(torch.diagonal(R))
+    del G, R
+    Q = Q32.double() * sgn.double()[None, :]
+    del Q32
+    Q /= torch.linalg.vector_norm(Q, dim=0)[None, :]
+    A = (Q * lam[None, :]) @ Q.T
+    del Q
+    A = 0.5 * (A + A.T)
+    sum_log = math.fsum(float(x) for x in torch.log(lam).cpu().tolist())
+    A = A.to(dtype)
+    if cache:
+        try:
+            os.makedirs(_cache_dir(), exist_ok=True)
+            tmp = path + f".tmp{os.getpid()}"
+            A.cpu().contiguous().numpy().tofile(tmp + ".bin")
+            with open(tmp + ".json", "w") as f:
+                json.dump({"sum_log": sum_log, "N": N, "seed": seed, "lo": lo, "hi": hi}, f)
+            os.replace(tmp + ".bin", path + ".bin")
+            os.replace(tmp + ".json", path + ".json")
+        except Exception:
+            pass
+    return A, sum_log
 
 
 def spd_reflectors_torch(N: int, seed: int, lo: float, hi: float, device, k: int = 8,
