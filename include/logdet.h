@@ -211,6 +211,34 @@ ld_status ld_logdet_backward_batched(const void* const* factors, int64_t count, 
                                      int64_t ldg, void* stream);
 
 /*
+ * Row-block condensation across processes (Sec. 2.1, Fig. 6): every process owns
+ * a block of rows; in turn, one process factors its next row as the pivot row
+ * and broadcasts it, and every process applies that step to its remaining rows.
+ * These two calls are the two halves of one step on the GPU; the schedule and
+ * the broadcast are the caller's (paper_1811_08057_gb300/dist.py,
+ * logdet_rowblock). Positions are those of the swap-to-boundary layout
+ * (Sec. 2.4); labels[q] = original column at position q, the same on every
+ * process.
+ *
+ * ld_rowblock_factor - the pivot row in place (device pointers):
+ *   row     m values in the storage type (dtype); on return row[j] = a_j / p for
+ *           j < m-1 after positions l and m-1 were exchanged, and row[m-1] = p
+ *   labels  device int32[m] (read only here)
+ *   step    device double[4]: out l, p, status (0 ok, 1 all-zero row, 2 NaN) and
+ *           labels[l]; l = argmax |a_j| with ties to the smallest label (Sec. 2.2)
+ * ld_rowblock_update - the step on `rows` rows of F (device, leading dimension
+ * ldf >= m): with l = step[0], positions l and m-1 exchanged, then
+ * a_ij <- fma(-a_il, r_j, a_ij) for j < m-1, the pivot column's entry a_il left
+ * at position m-1 (Eq. (2) with the factored row r, device, m-1 values); also
+ * exchanges labels[l] and labels[m-1]. Nothing when step[2] != 0.
+ * Both: LD_ERR_INVALID_ARG for NULL pointers, m < 1, ldf < m or an unknown dtype.
+ */
+ld_status ld_rowblock_factor(void* row, ld_dtype dtype, const int* labels, int64_t m,
+                             double* step, void* stream);
+ld_status ld_rowblock_update(void* F, ld_dtype dtype, int64_t rows, int64_t ldf, int64_t m,
+                             const void* r, int* labels, const double* step, void* stream);
+
+/*
  * Launch accounting for measurement (no counterpart in the paper). While on,
  * every kernel launch is counted per kernel class ("stage", "pivot_factor",
  * "update", "row_argmax", "finalize", ...) and launches of the class named by

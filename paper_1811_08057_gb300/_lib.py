@@ -39,6 +39,8 @@ LD_DTYPE_F32 = 1
 # ld_status
 STATUS = {0: "LD_OK", 1: "LD_ERR_INVALID_ARG", 2: "LD_ERR_UNSUPPORTED", 3: "LD_ERR_ALLOC",
           4: "LD_ERR_CUDA", 5: "LD_ERR_TIMEOUT"}
+LD_OK = 0
+LD_ERR_INVALID_ARG = 1
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -58,6 +60,8 @@ SIGNATURES = {
     "ld_logdet_backward_batched": ([_vp, _i64, _i64, _int, _vp, _vp, _i64, _vp], _int),
     "ld_rankb_update": ([_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _int),
     "ld_logdet_noalloc": ([_vp, _int, _i64, _i64, _vp, _pd, _pd], _int),
+    "ld_rowblock_factor": ([_vp, _int, _vp, _i64, _vp, _vp], _int),
+    "ld_rowblock_update": ([_vp, _int, _i64, _i64, _i64, _vp, _vp, _vp, _vp], _int),
     "ld_profile_start": ([ctypes.c_char_p], _int),
     "ld_profile_stop": ([], _int),
     "ld_profile_query": ([ctypes.c_char_p, _vp, _vp], _int),
@@ -124,6 +128,14 @@ def ld_logdet(A, a_dtype, n, lda, mode, stream, sign, logabs) -> int:
 def ld_logdet_variant(A, a_dtype, n, lda, mode, rule, side, stream, factors, sign, logabs) -> int:
     return load().ld_logdet_variant(A, a_dtype, n, lda, mode, rule, side, stream, factors, sign,
                                     logabs)
+
+
+def ld_rowblock_factor(row, dtype, labels, m, step, stream) -> int:
+    return load().ld_rowblock_factor(row, dtype, labels, m, step, stream)
+
+
+def ld_rowblock_update(F, dtype, rows, ldf, m, r, labels, step, stream) -> int:
+    return load().ld_rowblock_update(F, dtype, rows, ldf, m, r, labels, step, stream)
 
 
 def ld_factors_size(n, mode) -> int:
