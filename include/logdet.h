@@ -307,6 +307,8 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
  *                         next panel; exact arithmetic unchanged); >= 0
  *   "batched_kb_<k>"      panels of the batched sweep for matrices with n in
  *                         [64k, 64k+63] (k = 0..8; k = 8 also covers larger n): 8 or 16
+ *   "batched_threads"     threads per CTA of the FP32 batched sweep: 256 (default)
+ *                         or 128 (more CTAs per SM); results are the same bits
  *   "wait_limit_ns"       limit of the bounded waits of the grid-wide panel kernel
  *                         (LD_F64_BLOCKED's panels) on the current device, >= 0,
  *                         default 1e9; a wait that runs out flags the sweep, its

@@ -63,6 +63,7 @@ namespace {
 int g_blocked_b = 128;              // panel width of the blocked sweep (64 or 128)
 int64_t g_pair_min_n = 16384;       // pair the trailing updates of two panels from this n
 int g_batched_kb[kTuneBuckets] = {16, 16, 16, 16, 16, 16, 16, 16, 16};
+int g_batched_threads = 256;        // threads per CTA of the FP32 batched sweep (128 or 256)
 }  // namespace
 
 int tuned_blocked_b() {
@@ -76,6 +77,10 @@ int64_t tuned_pair_min_n() {
 const int* tuned_batched_kb() {
   tune_cache_autoload();
   return g_batched_kb;
+}
+int tuned_batched_threads() {
+  tune_cache_autoload();
+  return g_batched_threads;
 }
 
 ld_status tuning_set(const char* name, int64_t value) {
@@ -93,6 +98,11 @@ ld_status tuning_set(const char* name, int64_t value) {
   if (strcmp(name, "wait_limit_ns") == 0) {
     if (value < 0) return LD_ERR_INVALID_ARG;
     return set_panel_wait_limit((uint64_t)value);
+  }
+  if (strcmp(name, "batched_threads") == 0) {
+    if (value != 128 && value != 256) return LD_ERR_INVALID_ARG;
+    g_batched_threads = (int)value;
+    return LD_OK;
   }
   if (strncmp(name, "batched_kb_", 11) == 0) {
     char* end = nullptr;
@@ -120,6 +130,10 @@ ld_status tuning_get(const char* name, int64_t* value) {
     const ld_status st = get_panel_wait_limit(&ns);
     *value = (int64_t)ns;
     return st;
+  }
+  if (strcmp(name, "batched_threads") == 0) {
+    *value = g_batched_threads;
+    return LD_OK;
   }
   if (strncmp(name, "batched_kb_", 11) == 0) {
     char* end = nullptr;

@@ -26,7 +26,6 @@ namespace ld {
 
 namespace {
 
-constexpr int kBT = 256;  // threads per CTA
 constexpr int kKB = 16;   // pivots per panel
 
 struct BatchedArgs {
@@ -117,8 +116,10 @@ __device__ __forceinline__ void stage_col(const T* P, int pw, int j, int bb, flo
     *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
+// BT threads per CTA: 256, or 128 with more CTAs per SM (fewer warps take part
+// in each pivot's reductions and barriers).
+template <typename T, int BT>
+__global__ void __launch_bounds__(BT, sizeof(T) == 4 ? (BT == 128 ? 5 : 3) : 1)
     batched_kernel(BatchedArgs args, T* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_max = args.n_max;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
   int* label = reinterpret_cast<int*>(P + kKB * pw);          // n_max
   int* moved_dst = label + n_max;                             // 2 kKB
   int* moved_src = moved_dst + 2 * kKB;                       // 2 kKB
-  T* Cs = reinterpret_cast<T*>(                               // kKB x kBT multipliers (by pivot)
+  T* Cs = reinterpret_cast<T*>(                               // kKB x BT multipliers (by pivot)
       (reinterpret_cast<uintptr_t>(moved_src + 2 * kKB) + 15) & ~static_cast<uintptr_t>(15));
   __shared__ int s_mat, s_l, s_bad, s_nmoved;
   __shared__ double s_p;
@@ -137,8 +138,8 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
   __shared__ int s_xsrc[kKB], s_odst[kKB], s_osrc[kKB], s_nout;
   // FP32 pivot search: warp candidates, their columns and the boundary column
   // (by pivot parity)
-  __shared__ KCand wredk[2][kBT / 32];
-  __shared__ __align__(16) float wcolb[2][kBT / 32][kKB];
+  __shared__ KCand wredk[2][BT / 32];
+  __shared__ __align__(16) float wcolb[2][BT / 32][kKB];
   __shared__ __align__(16) float lcolb[2][kKB];
   __shared__ int lastlab[2];
 
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
     int* piv_p = rec ? rec_pivpos : (args.pp ? args.pp + (int64_t)mat * n_max : nullptr);
     // stage the matrix into the CTA's workspace (a0): a warp per row, eight
     // elements per lane in flight (the loads issued before the stores)
-    for (int i = warp; i < n; i += kBT / 32) {
+    for (int i = warp; i < n; i += BT / 32) {
       const int64_t ia = (int64_t)i * lda, iw = (int64_t)i * ldw;
       for (int j0 = lane; j0 < n; j0 += 256) {
         T v[8];
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           if (j0 + 32 * u < n) W[iw + j0 + 32 * u] = v[u];
       }
     }
-    for (int j = tid; j < n; j += kBT) label[j] = j;
+    for (int j = tid; j < n; j += BT) label[j] = j;
     const int kbm = args.kb_table[min(n / 64, kTuneBuckets - 1)];  // this matrix's panel depth
     double sign = 1.0, sum = 0.0, comp = 0.0;  // meaningful in thread 0
     int flags = 0;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
       const int m0 = n - s0;
       // panel rows into shared memory (a thread's column of the panel: loads
       // issued before the stores)
-      for (int j = tid; j < m0; j += kBT) {
+      for (int j = tid; j < m0; j += BT) {
         T v[kKB];
 #pragma unroll
         for (int t = 0; t < kKB; ++t) v[t] = (t < bb) ? W[(int64_t)(s0 + t) * ldw + j] : T(0);
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
       }
       __syncthreads();
       if constexpr (sizeof(T) == 4) {
-        // FP32: column ownership (thread x owns columns x, x + kBT, ...), one CTA
+        // FP32: column ownership (thread x owns columns x, x + BT, ...), one CTA
         // barrier per pivot; the pivots' sign and log-sum are left to the
         // finalize kernel (the same steps in pivot order)
         int bad = 0;
@@ -229,18 +230,18 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           const int par = t & 1;
           KCand cd;
           kc_init(cd);
-          for (int j = tid; j < m; j += kBT) kc_offer(cd, (float)P[t * pw + j], label[j], j);
+          for (int j = tid; j < m; j += BT) kc_offer(cd, (float)P[t * pw + j], label[j], j);
           const int src = kc_warp_best(cd);
           // columns staged with all loads issued before the stores
           if (lane == src && cd.key != 0u) stage_col(P, pw, kc_pos(cd), bb, wcolb[par][warp]);
-          if ((m - 1) % kBT == tid) {
+          if ((m - 1) % BT == tid) {
             stage_col(P, pw, m - 1, bb, lcolb[par]);
             lastlab[par] = label[m - 1];
           }
           if (lane == 0) wredk[par][warp] = cd;
           __syncthreads();
           KCand cb;
-          if (lane < kBT / 32)
+          if (lane < BT / 32)
             cb = wredk[par][lane];
           else
             kc_init(cb);
@@ -262,12 +263,12 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           const float* lc = lcolb[par];      // boundary column
           if (l != m - 1) {
             // exchange of columns l and m-1 (Sec. 2.4), each by its owner
-            if (l % kBT == tid) {
+            if (l % BT == tid) {
               for (int i = 0; i < bb; ++i)
                 if (i != t) P[i * pw + l] = (T)lc[i];
               label[l] = lastlab[par];
             }
-            if ((m - 1) % kBT == tid) {
+            if ((m - 1) % BT == tid) {
               for (int i = 0; i < bb; ++i) P[i * pw + m - 1] = (T)pc[i];
               label[m - 1] = cb.label;
             }
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
             pcv[i + 2] = q.z;
             pcv[i + 3] = q.w;
           }
-          for (int j = tid; j < m - 1; j += kBT) {
+          for (int j = tid; j < m - 1; j += BT) {
             const float v = (j == l) ? lc[t] : (float)P[t * pw + j];
             if (bb == kKB) {  // a full panel: pivot index and row range known statically
               switch (t) {
@@ -372,13 +373,13 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           // row t: factor (Eq. (3), Sec. 2.3) with the exchange of columns l and m-1
           // applied on the fly (Sec. 2.4); the boundary keeps the pivot. Other panel
           // rows: the exchange itself.
-          for (int j = tid; j < m - 1; j += kBT) {
+          for (int j = tid; j < m - 1; j += BT) {
             const T v = (j == l) ? P[t * pw + m - 1] : P[t * pw + j];
             P[t * pw + j] = (sizeof(T) == 4) ? (T)__fdiv_rn((float)v, (float)p) : (T)((double)v / p);
             if (j == l) P[t * pw + m - 1] = (T)p;
           }
           if (l != m - 1) {
-            for (int i = tid; i < bb; i += kBT) {
+            for (int i = tid; i < bb; i += BT) {
               if (i == t) continue;
               const T v = P[i * pw + l];
               P[i * pw + l] = P[i * pw + m - 1];
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           }
           __syncthreads();
           // rank-1 update of the remaining panel rows (Eq. (2)), one warp per row
-          for (int i = t + 1 + warp; i < bb; i += kBT / 32) {
+          for (int i = t + 1 + warp; i < bb; i += BT / 32) {
             const T ci = P[i * pw + m - 1];
             for (int j = lane; j < m - 1; j += 32) P[i * pw + j] = fma_t(-ci, P[t * pw + j], P[i * pw + j]);
           }
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
       if (s_bad) break;
       if (rec) {
         // the panel rows are final: factored rows r, pivots and multipliers
-        for (int e = tid; e < bb * m0; e += kBT) {
+        for (int e = tid; e < bb * m0; e += BT) {
           const int t = e / m0, j = e % m0;
           W[(int64_t)(s0 + t) * ldw + j] = P[t * pw + j];
         }
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
       if (rec) {
         // earlier (frozen) rows keep the layout of the record: the panel's
         // column exchanges reach them too
-        for (int i = warp; i < s0; i += kBT / 32) {
+        for (int i = warp; i < s0; i += BT / 32) {
           T* row = W + (int64_t)i * ldw;
           T mv = T(0);
           if (lane < nmoved) mv = row[moved_src[lane]];
@@ -471,13 +472,13 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
           __syncwarp();
         }
       }
-      // trailing rows, in chunks of kBT rows:
+      // trailing rows, in chunks of BT rows:
       //  phase 1 (one thread per row): the panel's composed column moves, then the
       //  row's kb multipliers by forward substitution in registers -> Cs;
       //  phase 2 (register tiles of 4 rows x 4 columns): the kb rank-1 updates in
       //  pivot order, one FMA per element per pivot (the per-pivot operations).
-      for (int r0 = s0 + bb; r0 < n; r0 += kBT) {
-        const int R = min(kBT, n - r0);
+      for (int r0 = s0 + bb; r0 < n; r0 += BT) {
+        const int R = min(BT, n - r0);
         if (tid < R) {
           T* row = W + (int64_t)(r0 + tid) * ldw;
           const int pb = m0 - bb;  // first position of the panel's pivot block
@@ -489,15 +490,15 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
 #pragma unroll
             for (int i = 0; i < kKB; i += 4) {
               const float4 q = *reinterpret_cast<const float4*>(row + pb + i);
-              Cs[(i + 0) * kBT + tid] = q.x;
-              Cs[(i + 1) * kBT + tid] = q.y;
-              Cs[(i + 2) * kBT + tid] = q.z;
-              Cs[(i + 3) * kBT + tid] = q.w;
+              Cs[(i + 0) * BT + tid] = q.x;
+              Cs[(i + 1) * BT + tid] = q.y;
+              Cs[(i + 2) * BT + tid] = q.z;
+              Cs[(i + 3) * BT + tid] = q.w;
             }
           } else {
 #pragma unroll
             for (int i = 0; i < kKB; ++i)
-              if (i < bb) Cs[i * kBT + tid] = row[pb + i];
+              if (i < bb) Cs[i * BT + tid] = row[pb + i];
           }
           // the panel's column moves (new[dst] = old[src]), reading old values
           // only: the multipliers (pivot t's column ends at m0-1-t) from the
@@ -508,14 +509,14 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
             x[t] = T(0);
             if (t < bb) {
               const int xs = s_xsrc[t];
-              x[t] = (xs >= pb) ? Cs[(xs - pb) * kBT + tid] : row[xs];
+              x[t] = (xs >= pb) ? Cs[(xs - pb) * BT + tid] : row[xs];
             }
           }
 #pragma unroll
           for (int k = 0; k < kKB; ++k)
             if (k < s_nout) {
               const int os = s_osrc[k];
-              row[s_odst[k]] = (os >= pb) ? Cs[(os - pb) * kBT + tid] : row[os];
+              row[s_odst[k]] = (os >= pb) ? Cs[(os - pb) * BT + tid] : row[os];
             }
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
 #pragma unroll
           for (int t = 0; t < kKB; ++t) {
             if (t < bb) {
-              Cs[t * kBT + tid] = x[t];
+              Cs[t * BT + tid] = x[t];
               if (rec) row[m0 - 1 - t] = x[t];  // multipliers (L) of this panel
             }
           }
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
         constexpr bool kPre = sizeof(T) == 4;
         T nxt[4][4];
         if (kPre && tid < ntile) load_tile(tid, nxt);
-        for (int tile = tid; tile < ntile; tile += kBT) {
+        for (int tile = tid; tile < ntile; tile += BT) {
           const int ri = (tile / nct) * 4, cj = (tile % nct) * 4;
           const bool full4 = cj + 4 <= ncols;
           T acc[4][4];
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
             for (int i = 0; i < 4; ++i)
 #pragma unroll
               for (int j = 0; j < 4; ++j) acc[i][j] = nxt[i][j];
-            if (tile + kBT < ntile) load_tile(tile + kBT, nxt);
+            if (tile + BT < ntile) load_tile(tile + BT, nxt);
           } else {
             load_tile(tile, acc);
           }
@@ -580,13 +581,13 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
             if (t < bb) {
               T cv[4], rv[4];
               if constexpr (sizeof(T) == 4) {
-                const float4 c4 = *reinterpret_cast<const float4*>(Cs + t * kBT + ri);
+                const float4 c4 = *reinterpret_cast<const float4*>(Cs + t * BT + ri);
                 const float4 r4 = *reinterpret_cast<const float4*>(P + t * pw + cj);
                 cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
                 rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
               } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) cv[i] = Cs[t * kBT + ri + i];
+                for (int i = 0; i < 4; ++i) cv[i] = Cs[t * BT + ri + i];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) rv[j] = P[t * pw + cj + j];
               }
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 3 : 1)
       }
     }
     if (rec)
-      for (int j = tid; j < n; j += kBT) rec_colperm[j] = label[j];
+      for (int j = tid; j < n; j += BT) rec_colperm[j] = label[j];
     __syncthreads();
   }
 }
@@ -753,28 +754,27 @@ __global__ void batched_finalize_kernel(const int64_t* __restrict__ n_arr, int c
   }
 }
 
-template <typename T>
-ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+template <typename T, int BT>
+ld_status run_batched_bt(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
                       const int64_t* lda, int64_t count, int64_t n_max, double* signs,
                       double* logabs, void* const* factors, ld_mode mode, cudaStream_t stream) {
   const int64_t ldw = (int64_t)align_up((size_t)std::max<int64_t>(n_max, 1), 4);
   const size_t smem = (size_t)kKB * batched_pitch(n_max) * sizeof(T) + (size_t)n_max * 4 +
-                      4 * kKB * 4 + 16 + (size_t)kBT * kKB * sizeof(T) + 64;
+                      4 * kKB * 4 + 16 + (size_t)BT * kKB * sizeof(T) + 64;
   if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
-  static size_t smem_set[2] = {0, 0};
-  const int ti = sizeof(T) == 8;
-  if (smem > 48 * 1024 && smem_set[ti] < smem) {
-    if (cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static size_t smem_set = 0;  // one per instantiation
+  if (smem > 48 * 1024 && smem_set < smem) {
+    if (cudaFuncSetAttribute(batched_kernel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return LD_ERR_CUDA;
-    smem_set[ti] = smem;
+    smem_set = smem;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, kBT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T, BT>, BT, smem) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  per_sm = std::min(per_sm, 4);
+  per_sm = std::min(per_sm, BT == 128 ? 6 : 4);
   const int64_t grid = std::min<int64_t>((int64_t)device_sm_count() * per_sm, count);
   const size_t ws_bytes = factors ? 0 : (size_t)grid * n_max * ldw * sizeof(T);
   const bool f32 = sizeof(T) == 4;
@@ -822,7 +822,7 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
     const int* kbt = tuned_batched_kb();
     for (int k = 0; k < kTuneBuckets; ++k) a.kb_table[k] = std::min(kKB, std::max(1, kbt[k]));
     ProfScope ps("batched", stream);
-    batched_kernel<T><<<(unsigned)grid, kBT, smem, stream>>>(a, factors ? nullptr : ws);
+    batched_kernel<T, BT><<<(unsigned)grid, BT, smem, stream>>>(a, factors ? nullptr : ws);
     if (cudaGetLastError() != cudaSuccess) st = LD_ERR_CUDA;
   }
   if (st == LD_OK && f32) {
@@ -840,6 +840,19 @@ ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t
   }
   scratch_free(scratch, stream);
   return st;
+}
+
+template <typename T>
+ld_status run_batched(const void* const* A_ptrs, ld_dtype a_dtype, const int64_t* n,
+                      const int64_t* lda, int64_t count, int64_t n_max, double* signs,
+                      double* logabs, void* const* factors, ld_mode mode, cudaStream_t stream) {
+  if constexpr (sizeof(T) == 4) {
+    if (tuned_batched_threads() == 128)
+      return run_batched_bt<T, 128>(A_ptrs, a_dtype, n, lda, count, n_max, signs, logabs, factors,
+                                    mode, stream);
+  }
+  return run_batched_bt<T, 256>(A_ptrs, a_dtype, n, lda, count, n_max, signs, logabs, factors,
+                                mode, stream);
 }
 
 }  // namespace

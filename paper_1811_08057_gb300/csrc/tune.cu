@@ -8,7 +8,8 @@
 //                  largest size asked for (at most 32768);
 //   plain modes    panel depth of the batched sweep in {8, 16} for every size
 //                  class present (batched_kb_<k>), timed on a batch of up to 256
-//                  matrices of the class's largest size.
+//                  matrices of the class's largest size; for FP32, the CTA width
+//                  in {256, 128} (batched_threads) on the largest class's batch.
 // The synthetic matrices are a_ij = u_ij / sqrt(n) + 2 [i == j] with u_ij
 // uniform in [-1, 1) from a counter-based hash of (seed, i, j) (splitmix64):
 // dense, nonsingular, and reproducible on any device.
@@ -101,10 +102,11 @@ std::string cache_file() {
   return std::string(dir) + "/" + name + ".tune";
 }
 
-const char* table_names[2 + kTuneBuckets] = {
-    "blocked_b",      "blocked_pair_min_n", "batched_kb_0", "batched_kb_1", "batched_kb_2",
-    "batched_kb_3",   "batched_kb_4",       "batched_kb_5", "batched_kb_6", "batched_kb_7",
-    "batched_kb_8"};
+constexpr int kTableSize = 3 + kTuneBuckets;
+const char* table_names[kTableSize] = {
+    "blocked_b",    "blocked_pair_min_n", "batched_threads", "batched_kb_0", "batched_kb_1",
+    "batched_kb_2", "batched_kb_3",       "batched_kb_4",    "batched_kb_5", "batched_kb_6",
+    "batched_kb_7", "batched_kb_8"};
 
 ld_status tune_blocked(const std::vector<int64_t>& sizes, ld_mode mode, cudaStream_t stream) {
   const int64_t n = std::min<int64_t>(*std::max_element(sizes.begin(), sizes.end()), 32768);
@@ -164,6 +166,9 @@ ld_status tune_batched(const std::vector<int64_t>& sizes, ld_mode mode, cudaStre
     ++members[k];
   }
   const size_t es = mode == LD_F64_PLAIN ? 8 : 4;
+  int k_top = -1;  // the size class of the largest matrices: it also picks the CTA width
+  for (int k = 0; k < kTuneBuckets; ++k)
+    if (largest[k] >= 2) k_top = k;
   ld_status st = LD_OK;
   for (int k = 0; k < kTuneBuckets && st == LD_OK; ++k) {
     const int64_t n = largest[k];
@@ -212,6 +217,28 @@ ld_status tune_batched(const std::vector<int64_t>& sizes, ld_mode mode, cudaStre
       }
     }
     tuning_set(name.c_str(), st == LD_OK ? best_kb : old);
+    if (k == k_top && es == 4 && st == LD_OK) {
+      int64_t old_bt = 256;
+      tuning_get("batched_threads", &old_bt);
+      double best_t = 1e300;
+      int64_t best_bt = old_bt;
+      for (int64_t bt : {256, 128}) {
+        if (st != LD_OK) break;
+        tuning_set("batched_threads", bt);
+        double ms = 0.0;
+        st = time_ms(
+            [&]() {
+              return ld_logdet_batched(ptrs, LD_DTYPE_F32, ns, ldas, count, n, mode, stream, res,
+                                       res + count);
+            },
+            stream, 2, &ms);
+        if (st == LD_OK && ms < best_t) {
+          best_t = ms;
+          best_bt = bt;
+        }
+      }
+      tuning_set("batched_threads", st == LD_OK ? best_bt : old_bt);
+    }
     scratch_free(buf, stream);
   }
   return st;
@@ -261,12 +288,12 @@ extern "C" ld_status ld_tune_load(const char* path) {
   while ((got = fscanf(fp, "%63s %lld", name, &v)) == 2) entries.emplace_back(name, v);
   if (got != EOF) ok = false;
   fclose(fp);
-  int64_t saved[2 + kTuneBuckets];
-  for (int i = 0; i < 2 + kTuneBuckets; ++i) tuning_get(table_names[i], &saved[i]);
+  int64_t saved[kTableSize];
+  for (int i = 0; i < kTableSize; ++i) tuning_get(table_names[i], &saved[i]);
   for (auto& e : entries)
     if (ok && tuning_set(e.first.c_str(), e.second) != LD_OK) ok = false;
   if (!ok)
-    for (int i = 0; i < 2 + kTuneBuckets; ++i) tuning_set(table_names[i], saved[i]);
+    for (int i = 0; i < kTableSize; ++i) tuning_set(table_names[i], saved[i]);
   return ok ? LD_OK : LD_ERR_INVALID_ARG;
 }
 

@@ -19,17 +19,20 @@ def test_save_load_round_trip(tmp_path, saved_table):
     assert _lib.ld_set_tuning("blocked_b", 64) == 0
     assert _lib.ld_set_tuning("blocked_pair_min_n", 12345) == 0
     assert _lib.ld_set_tuning("batched_kb_3", 8) == 0
+    assert _lib.ld_set_tuning("batched_threads", 128) == 0
     want = tune.table()
     tune.save(path)
     text = open(path).read().split()
     assert text[0:2] == ["blocked_b", "64"]
+    scramble = {"blocked_b": 128, "batched_threads": 256}
     for nm in tune.NAMES:  # scramble, then load
-        assert _lib.ld_set_tuning(nm, 128 if nm == "blocked_b" else 16) == 0
+        assert _lib.ld_set_tuning(nm, scramble.get(nm, 16)) == 0
     tune.load(path)
     assert tune.table() == want
 
 
 @pytest.mark.parametrize("bad", ["blocked_b 96\n", "no_such_entry 1\n", "batched_kb_9 8\n",
+                                 "batched_threads 192\n",
                                  "blocked_b 64\nbatched_kb_x 8\n", "blocked_b sixty-four\n"])
 def test_bad_file_leaves_table(tmp_path, saved_table, bad):
     path = tmp_path / "bad.tune"

@@ -36,6 +36,19 @@ def test_batched_results_independent_of_panel_depth(saved_table):
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
 
+def test_batched_results_independent_of_cta_width(saved_table):
+    sizes = [32, 77, 130, 256, 300, 511]
+    mats = [torch.from_numpy(workloads.dense_gaussian(n, seed=n + 1)).float().cuda() for n in sizes]
+    outs = []
+    for bt in (256, 128):
+        assert _lib.ld_set_tuning("batched_threads", bt) == 0
+        s, l = api.logdet_batched(mats, "f32_plain")
+        outs.append((s.clone(), l.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    s1, l1 = api.logdet(mats[3], "f32_plain")
+    assert float(outs[1][0][3]) == float(s1) and float(outs[1][1][3]) == float(l1)
+
+
 def test_ld_tune_blocked_and_batched(tmp_path, monkeypatch, saved_table):
     monkeypatch.setenv("LD_TUNE_CACHE", str(tmp_path))
     t = tune.autotune([3000], "f32_3xtf32")
@@ -44,6 +57,7 @@ def test_ld_tune_blocked_and_batched(tmp_path, monkeypatch, saved_table):
     t = tune.autotune([40, 130, 300, 520], "f32_plain")
     for k in (0, 2, 4, 8):
         assert t[f"batched_kb_{k}"] in (8, 16)
+    assert t["batched_threads"] in (128, 256)
     files = os.listdir(tmp_path)
     assert len(files) == 1 and files[0].endswith(".tune")
     # a fresh process with the cache directory set starts from the stored table
