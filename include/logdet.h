@@ -52,7 +52,13 @@ typedef enum {
                          (the N = 8000 iid Gaussian matrix does); no sign or
                          accuracy guarantee */
   LD_F32_3XTF32 = 4,  /* FP32 storage, panels + split-TF32 (hi*hi+hi*lo+lo*hi) */
-  LD_F32_BF16X3 = 5   /* FP32 storage, panels + split-BF16 (hi*hi+hi*lo+lo*hi) */
+  LD_F32_BF16X3 = 5,  /* FP32 storage, panels + split-BF16 (hi*hi+hi*lo+lo*hi) */
+  LD_F64_OZAKI = 6    /* FP64 storage, panels + FP64-accurate rank-b update on the
+                         BF16 tensor cores: each operand row cut into six 8-bit
+                         slices under a common exponent (Ozaki-style error-free
+                         splitting), the slice products accumulated exactly in
+                         FP32, summed in FP64 (truncation 2^-47 of a row's
+                         largest entry; not bit-identical to FP64 FMAs) */
 } ld_mode;
 
 /* Element type of an input matrix. */
@@ -263,13 +269,19 @@ ld_status ld_profile_classes(char* buf, int64_t cap);
  *   D[M x N] -= A[M x K] * B[N x K]^T
  * (block condensation, the paper's future-work extension of Eq. (2)).
  *   mode   LD_F64_BLOCKED: FP64 A, B, D, FP64 FMAs on the CUDA cores;
+ *          LD_F64_OZAKI: FP64 A, B, D; each row of A and of B cut into six
+ *          8-bit slices under the row's exponent (exact), the 21 slice products
+ *          of order <= 5 on the BF16 tensor cores with exact FP32 accumulation,
+ *          summed and applied in FP64, in passes of at most 128 along K
+ *          (Ozaki, Ogita, Oishi and Rump's error-free splitting);
  *          LD_F32_TF32 / LD_F32_3XTF32 / LD_F32_BF16X3: FP32 A, B, D, products on
  *          the tensor cores (tcgen05, TMA-fed) with FP32 accumulation, operands
  *          used as TF32, split hi+lo at TF32, or split hi+lo at BF16
  *          (hi*hi + hi*lo + lo*hi)
  *   A, B, D  device, row-major, leading dimensions lda >= K, ldb >= K, ldd >= N;
- *          for the tensor-core modes K must be a multiple of 64 (else
- *          LD_ERR_UNSUPPORTED)
+ *          for the FP32 tensor-core modes K must be a multiple of 64 (else
+ *          LD_ERR_UNSUPPORTED); LD_F64_OZAKI takes any K and any alignment (its
+ *          sliced operands are internal copies)
  * Allocates stream-ordered scratch and waits for `stream` before returning (to
  * report LD_ERR_TIMEOUT from a device wait).
  */

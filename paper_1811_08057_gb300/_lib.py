@@ -22,6 +22,7 @@ LD_F32_PLAIN = 2
 LD_F32_TF32 = 3
 LD_F32_3XTF32 = 4
 LD_F32_BF16X3 = 5
+LD_F64_OZAKI = 6
 MODES = {
     "f64_plain": LD_F64_PLAIN,
     "f64_blocked": LD_F64_BLOCKED,
@@ -29,7 +30,9 @@ MODES = {
     "f32_tf32": LD_F32_TF32,
     "f32_3xtf32": LD_F32_3XTF32,
     "f32_bf16x3": LD_F32_BF16X3,
+    "f64_ozaki": LD_F64_OZAKI,
 }
+F64_MODES = (LD_F64_PLAIN, LD_F64_BLOCKED, LD_F64_OZAKI)
 # ld_pivot_rule, ld_factor_side
 PIVOT_RULES = {"max_abs": 0, "closest_to_one": 1, "first_nonzero": 2}
 FACTOR_SIDES = {"row": 0, "column": 1}

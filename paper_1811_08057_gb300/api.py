@@ -121,7 +121,7 @@ def _align(x, a=256):
 
 def parse_factors(record: torch.Tensor, n: int, mode) -> Factors:
     mode = _mode_code(mode)
-    f64 = mode in (_lib.LD_F64_PLAIN, _lib.LD_F64_BLOCKED)
+    f64 = mode in _lib.F64_MODES
     es = 8 if f64 else 4
     ldf = _align(max(n, 1), 32)
     off = 256
@@ -222,7 +222,7 @@ def logdet_backward(f: Factors, g=1.0, stream=None) -> torch.Tensor:
     """G = g * A^{-T} from a factor record (ld_logdet_backward)."""
     dev = f.record.device
     gt = torch.as_tensor(g, dtype=torch.float64, device=dev).reshape(1).contiguous()
-    dt = torch.float64 if f.mode in (_lib.LD_F64_PLAIN, _lib.LD_F64_BLOCKED) else torch.float32
+    dt = torch.float64 if f.mode in _lib.F64_MODES else torch.float32
     G = torch.empty(f.n, f.n, dtype=dt, device=dev)
     code = _lib.ld_logdet_backward(f.record.data_ptr(), gt.data_ptr(), G.data_ptr(), max(f.n, 1),
                                    _stream_handle(stream))
@@ -246,7 +246,7 @@ class LogAbsDet(torch.autograd.Function):
         n = A.shape[-1]
         dev = A.device
         if batched:
-            if mode_c == _lib.LD_F64_BLOCKED:
+            if mode_c in (_lib.LD_F64_BLOCKED, _lib.LD_F64_OZAKI):
                 raise ValueError("batched forward supports f64_plain, f32_plain and the FP32 "
                                  "tensor-core modes")
             mats = [M.contiguous() for M in mats]
@@ -277,7 +277,7 @@ class LogAbsDet(torch.autograd.Function):
         _, recs, _ = ctx.keep
         dev = grad_out.device
         g = grad_out.detach().to(torch.float64).reshape(count).contiguous()
-        sdt = torch.float64 if mode_c in (_lib.LD_F64_PLAIN, _lib.LD_F64_BLOCKED) else torch.float32
+        sdt = torch.float64 if mode_c in _lib.F64_MODES else torch.float32
         G = torch.empty(count, n, n, dtype=sdt, device=dev)
         gptrs = torch.tensor([G[i].data_ptr() for i in range(count)], dtype=torch.int64,
                              device=dev)

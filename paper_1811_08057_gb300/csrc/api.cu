@@ -153,6 +153,7 @@ static ld_status run_sweep(const void* A, ld_dtype a_dtype, int64_t lda, const R
     case LD_F32_PLAIN:
       return run_plain<float>(A, a_dtype, lda, r, keep, stream);
     case LD_F64_BLOCKED:
+    case LD_F64_OZAKI:
     case LD_F32_TF32:
     case LD_F32_3XTF32:
     case LD_F32_BF16X3:

@@ -388,7 +388,7 @@ struct OpBuf {
 };
 
 size_t op_elem_bytes(ld_mode mode) {
-  return mode == LD_F64_BLOCKED ? 8 : mode == LD_F32_BF16X3 ? 2 : 4;
+  return mode_is_f64(mode) ? 8 : mode == LD_F32_BF16X3 ? 2 : 4;
 }
 bool op_split(ld_mode mode) { return mode == LD_F32_3XTF32 || mode == LD_F32_BF16X3; }
 size_t op_bytes(ld_mode mode, int64_t cap, int64_t bb) {
@@ -476,13 +476,22 @@ ld_status launch_transpose(ld_mode mode, const T* F, int64_t ldf, int64_t s0, in
 }
 
 // Trailing update D[M x ncols] -= A B^T with the operands already in the mode's
-// format: rows [r0, r0 + M) of the A buffer, the whole B buffer.
+// format: rows [r0, r0 + M) of the A buffer, the whole B buffer. LD_F64_OZAKI:
+// the A rows are sliced here (into the same rows of asl); bsl holds B's slices.
 template <typename T>
 ld_status trailing_update(ld_mode mode, int64_t M, int64_t ncols, int64_t bb, const OpBuf& a,
                           int64_t r0, const OpBuf& bo, T* D, int64_t ldd, int* err,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, const OzOperand* asl = nullptr,
+                          const OzOperand* bsl = nullptr) {
   if (M <= 0 || ncols <= 0) return LD_OK;
   const size_t off = (size_t)r0 * bb * a.es;
+  if (mode == LD_F64_OZAKI) {
+    if (!asl || !bsl) return LD_ERR_INVALID_ARG;
+    const OzOperand ar = ozaki_rows(*asl, r0);
+    ld_status st = ozaki_split(M, bb, reinterpret_cast<const double*>(a.hi + off), bb, ar, stream);
+    if (st != LD_OK) return st;
+    return ozaki_gemm(ar, *bsl, M, ncols, reinterpret_cast<double*>(D), ldd, err, stream);
+  }
   if (mode == LD_F64_BLOCKED)
     return rankb_update(mode, M, ncols, bb, a.hi + off, bb, bo.hi, bb, D, ldd, nullptr, err, stream);
   const TcOperand oa{a.hi + off, a.lo ? a.lo + off : nullptr, bb, 0};
@@ -542,8 +551,11 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   // A and B operands by panel parity (by step modulo 4 when pairing): the
   // low-priority stream may still read earlier steps' while the critical stream
   // writes the current one's
+  // LD_F64_OZAKI: the operands' slices, by panel parity like the operands
+  const bool ozaki = r.mode == LD_F64_OZAKI;
+  const size_t ozb = ozaki ? align_up(ozaki_operand_bytes(n, b), kAlign) : 0;
   const size_t scratch_bytes =
-      grid_panel_bytes + nbuf * cl_bytes + 2 * nbuf * opb + perm_bytes + 2 * kAlign;
+      grid_panel_bytes + nbuf * cl_bytes + 2 * nbuf * opb + 2 * nbuf * ozb + perm_bytes + 2 * kAlign;
   void* scratch = nullptr;
   st = scratch_alloc(&scratch, scratch_bytes, stream);
   if (st != LD_OK) return st;
@@ -561,6 +573,15 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     p += opb;
     bbuf[q] = op_buf(r.mode, p, n, b);
     p += opb;
+  }
+  OzOperand asl[2] = {}, bsl[2] = {};
+  if (ozaki) {
+    for (int q = 0; q < 2; ++q) {
+      asl[q] = ozaki_operand(p, n, b);
+      p += ozb;
+      bsl[q] = ozaki_operand(p, n, b);
+      p += ozb;
+    }
   }
   void* perm_tmp = p;
   T* F = static_cast<T*>(r.F);
@@ -713,6 +734,8 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     const int* mv = used_cluster ? moves : nullptr;
     st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb, s0 + bb + nb, abuf[par], mv, hi);
     if (st == LD_OK) st = launch_transpose<T>(r.mode, F, r.ldf, s0, bb, ncols, bbuf[par], hi);
+    if (st == LD_OK && ozaki)
+      st = ozaki_split(ncols, bb, reinterpret_cast<const double*>(bbuf[par].hi), bb, bsl[par], hi);
     if (st != LD_OK) break;
     // the remaining rows on lo: moves, multipliers and update, overlapping the
     // next panel (they need this panel's moves and B, both on hi by now)
@@ -725,13 +748,14 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
         st = launch_trsm<T>(r.mode, F, r.ldf, s0, bb, m0, s0 + bb + nb, n, arest, mv, lo);
       if (st == LD_OK)
         st = trailing_update<T>(r.mode, rest, ncols, bb, abuf[par], nb, bbuf[par],
-                                F + (s0 + bb + nb) * r.ldf, r.ldf, err, lo);
+                                F + (s0 + bb + nb) * r.ldf, r.ldf, err, lo, &asl[par & 1],
+                                &bsl[par & 1]);
       if (st != LD_OK) break;
       rest_pending = true;
     }
     // the next panel's rows on hi
     st = trailing_update<T>(r.mode, nb, ncols, bb, abuf[par], 0, bbuf[par], F + (s0 + bb) * r.ldf,
-                            r.ldf, err, hi);
+                            r.ldf, err, hi, &asl[par & 1], &bsl[par & 1]);
   }
   // join every stream back into the caller's stream
   const ld_status j1 = link(hi, stream, ev[0]);
@@ -833,7 +857,7 @@ ld_status run_blocked_batched(const void* const* A_ptrs, ld_dtype a_dtype, const
 
 ld_status run_blocked(const void* A, ld_dtype a_dtype, int64_t lda, const Record& r,
                       bool keep_factors, cudaStream_t stream) {
-  if (r.mode == LD_F64_BLOCKED)
+  if (mode_is_f64(r.mode))
     return run_blocked_t<double>(A, a_dtype, lda, r, keep_factors, stream);
   return run_blocked_t<float>(A, a_dtype, lda, r, keep_factors, stream);
 }

@@ -529,10 +529,12 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 // K-major operand as a 3-D TMA map: `batch` matrices `bstride` elements apart,
-// each rows x K with leading dimension ld (elements), boxes of 128 bytes x
-// box_rows rows with the 128-byte swizzle. Loads past rows / K read zeros.
-bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, int batch,
-              int64_t bstride, int es, int box_rows) {
+// each rows x K with leading dimension ld (elements), boxes of `swizzle` bytes
+// (128 or 64) x box_rows rows with the swizzle of that width. Loads past rows / K
+// read zeros.
+bool make_map_swizzled(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, int batch,
+                       int64_t bstride, int es, int box_rows, int swizzle) {
+  if (swizzle != 128 && swizzle != 64) return false;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((size_t)ld * es) % 16 != 0 ||
@@ -541,13 +543,19 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, i
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
   cuuint64_t strides[2] = {(cuuint64_t)ld * es,
                            (cuuint64_t)(batch > 1 ? bstride : (int64_t)rows * ld) * es};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(swizzle / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    3, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, int batch,
+              int64_t bstride, int es, int box_rows) {
+  return make_map_swizzled(map, base, rows, K, ld, batch, bstride, es, box_rows, 128);
 }
 
 namespace {
@@ -639,6 +647,11 @@ ld_status launch_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K,
 // Bytes of scratch needed by rankb_update for an M x N x K update in `mode`.
 size_t rankb_scratch_bytes(ld_mode mode, int64_t M, int64_t N, int64_t K) {
   if (mode == LD_F64_BLOCKED) return kAlign;
+  if (mode == LD_F64_OZAKI) {
+    const int64_t kc = std::min<int64_t>(K, 128);
+    return align_up(ozaki_operand_bytes(M, kc), kAlign) + align_up(ozaki_operand_bytes(N, kc), kAlign) +
+           kAlign;
+  }
   const size_t es = (mode == LD_F32_BF16X3) ? 2 : 4;
   const size_t parts = (mode == LD_F32_TF32) ? 1 : 2;
   return align_up((size_t)M * K * es, kAlign) * parts + align_up((size_t)N * K * es, kAlign) * parts +
@@ -660,6 +673,21 @@ ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void
                                                static_cast<const double*>(B), ldb,
                                                static_cast<double*>(D), ldd, (int)M, (int)N, (int)K);
     LD_CHECK_LAUNCH();
+    return LD_OK;
+  }
+  if (mode == LD_F64_OZAKI) {
+    // passes of at most 128 along K, each sliced and applied to D in turn
+    const int64_t kc = std::min<int64_t>(K, 128);
+    char* p = static_cast<char*>(scratch);
+    const OzOperand sa = ozaki_operand(p, M, kc);
+    const OzOperand sb = ozaki_operand(p + align_up(ozaki_operand_bytes(M, kc), kAlign), N, kc);
+    for (int64_t k0 = 0; k0 < K; k0 += 128) {
+      const int64_t kk = std::min<int64_t>(128, K - k0);
+      ld_status st = ozaki_split(M, kk, static_cast<const double*>(A) + k0, lda, sa, stream);
+      if (st == LD_OK) st = ozaki_split(N, kk, static_cast<const double*>(B) + k0, ldb, sb, stream);
+      if (st == LD_OK) st = ozaki_gemm(sa, sb, M, N, static_cast<double*>(D), ldd, err, stream);
+      if (st != LD_OK) return st;
+    }
     return LD_OK;
   }
   if (K % 64 != 0) return LD_ERR_UNSUPPORTED;
@@ -761,7 +789,7 @@ extern "C" ld_status ld_rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t
   if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldd < N) return LD_ERR_INVALID_ARG;
   if (M == 0 || N == 0 || K == 0) return LD_OK;
   if (!A || !B || !D) return LD_ERR_INVALID_ARG;
-  if (mode != LD_F64_BLOCKED && K % 64 != 0) return LD_ERR_UNSUPPORTED;
+  if (!mode_is_f64(mode) && K % 64 != 0) return LD_ERR_UNSUPPORTED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   void* scratch = nullptr;
   ld_status st = scratch_alloc(&scratch, rankb_scratch_bytes(mode, M, N, K) + 2 * kAlign, stream);

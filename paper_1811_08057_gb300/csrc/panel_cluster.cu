@@ -582,7 +582,7 @@ size_t panel_cluster_scratch_bytes() {
 // back).
 ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
                                void* scratch, bool defer_logsum, cudaStream_t stream) {
-  if (r.mode == LD_F64_BLOCKED || bb > kBMax) return LD_ERR_UNSUPPORTED;
+  if (mode_is_f64(r.mode) || bb > kBMax) return LD_ERR_UNSUPPORTED;
   const int64_t m0 = r.n - s0;
   static int cl_ok = -1;  // cluster size that formed before (16 or 8), 0 = none
   if (cl_ok == 0) return LD_ERR_UNSUPPORTED;

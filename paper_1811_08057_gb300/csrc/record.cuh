@@ -12,11 +12,13 @@ constexpr size_t kAlign = 256;
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-inline bool mode_valid(int mode) { return mode >= LD_F64_PLAIN && mode <= LD_F32_BF16X3; }
-inline bool mode_is_f64(ld_mode mode) { return mode == LD_F64_PLAIN || mode == LD_F64_BLOCKED; }
+inline bool mode_valid(int mode) { return mode >= LD_F64_PLAIN && mode <= LD_F64_OZAKI; }
+inline bool mode_is_f64(ld_mode mode) {
+  return mode == LD_F64_PLAIN || mode == LD_F64_BLOCKED || mode == LD_F64_OZAKI;
+}
 inline bool mode_is_blocked(ld_mode mode) {
-  return mode == LD_F64_BLOCKED || mode == LD_F32_TF32 || mode == LD_F32_3XTF32 ||
-         mode == LD_F32_BF16X3;
+  return mode == LD_F64_BLOCKED || mode == LD_F64_OZAKI || mode == LD_F32_TF32 ||
+         mode == LD_F32_3XTF32 || mode == LD_F32_BF16X3;
 }
 inline int64_t leading_dim(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), 32); }
 
@@ -174,6 +176,26 @@ size_t rankb_operand_bytes(ld_mode mode, int64_t rows, int64_t K);
 // dst (rankb_operand_bytes bytes) and describes it in *op.
 ld_status rankb_prepare(ld_mode mode, int64_t rows, int64_t K, const float* src, int64_t ld,
                         void* dst, TcOperand* op, cudaStream_t stream);
+// ---- FP64-accurate update on the BF16 tensor cores (gemm_ozaki.cu) ----
+// Sliced operand: cap rows of kp BF16 values per slice (slice s at sl + s * cap *
+// kp), the row exponents ex[cap]; rows taken from r0 on with ozaki_rows.
+struct OzOperand {
+  uint16_t* sl;
+  int* ex;
+  int64_t cap;
+  int64_t kp;
+};
+int64_t ozaki_kpad(int64_t K);                       // K rounded up to the 32-element chunk
+size_t ozaki_operand_bytes(int64_t rows, int64_t K);  // slices and exponents of rows x K
+OzOperand ozaki_operand(void* base, int64_t rows, int64_t K);
+OzOperand ozaki_rows(const OzOperand& o, int64_t r0);
+// Slices of rows x K FP64 values (rows ld apart) into dst's rows [0, rows).
+ld_status ozaki_split(int64_t rows, int64_t K, const double* src, int64_t ld, const OzOperand& dst,
+                      cudaStream_t stream);
+// D[M x N] -= A B^T from sliced operands (rows [0, M) of a, [0, N) of b; K <= 128).
+ld_status ozaki_gemm(const OzOperand& a, const OzOperand& b, int64_t M, int64_t N, double* D,
+                     int64_t ldd, int* err, cudaStream_t stream);
+
 ld_status rankb_update(ld_mode mode, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                        const void* B, int64_t ldb, void* D, int64_t ldd, void* scratch, int* err,
                        cudaStream_t stream);

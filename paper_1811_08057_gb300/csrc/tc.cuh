@@ -8,6 +8,13 @@
 #include "common.cuh"
 
 namespace ld {
+
+// 3-D TMA map of a K-major operand (gemm_tc.cu): `batch` matrices `bstride`
+// elements apart, each rows x K (leading dimension ld elements), boxes of
+// `swizzle` bytes (128 or 64) x box_rows rows in the swizzle of that width.
+bool make_map_swizzled(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, int batch,
+                       int64_t bstride, int es, int box_rows, int swizzle);
+
 namespace tc {
 
 // A bounded wait gives up after this many nanoseconds of %globaltimer.

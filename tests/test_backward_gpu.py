@@ -22,7 +22,8 @@ def rel_fro(G, R):
 
 
 @pytest.mark.parametrize("mode,tol", [("f64_plain", 1e-10), ("f32_plain", 1e-4),
-                                      ("f64_blocked", 1e-10), ("f32_3xtf32", 1e-4)])
+                                      ("f64_blocked", 1e-10), ("f64_ozaki", 1e-10),
+                                      ("f32_3xtf32", 1e-4)])
 @pytest.mark.parametrize("n", [1, 2, 5, 64, 129, 300])
 def test_backward_matches_fp64_inverse(mode, tol, n):
     A = workloads.dense_gaussian(n, seed=500 + n) + 3.0 * np.eye(n)

@@ -2,8 +2,9 @@
 
 Exactly representable inputs (workloads.dyadic_lu): every mode takes the oracle's
 pivot sequence exactly and returns the exact sign and log|det|. Gaussian inputs:
-sign exact; log|det| within the stated relative tolerance (FP64 blocked 1e-12,
-3xTF32 1e-5, BF16x3 1e-4); plain TF32 is reported against a loose bound only.
+sign exact; log|det| within the stated relative tolerance (FP64 blocked and the
+FP64-accurate sliced tensor-core update 1e-12, 3xTF32 1e-5, BF16x3 1e-4); plain
+TF32 is reported against a loose bound only.
 """
 import json
 import math
@@ -19,7 +20,8 @@ from paper_1811_08057_gb300 import api
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64_blocked": 1e-12, "f32_3xtf32": 1e-5, "f32_bf16x3": 1e-4, "f32_tf32": 2e-2}
+TOL = {"f64_blocked": 1e-12, "f64_ozaki": 1e-12, "f32_3xtf32": 1e-5, "f32_bf16x3": 1e-4,
+       "f32_tf32": 2e-2}
 # BF16x3 carries each FP32 operand as two BF16 pieces (16 significant bits), so
 # every product of the trailing update is off by up to 2^-16 relative; the FP32
 # accumulation is not the limit (test_rankb_gpu.test_bf16x3_error_is_the_split).
@@ -74,17 +76,19 @@ def test_blocked_factors_reconstruct(mode):
     U = np.triu(FJ, 1) + np.eye(n)
     cp = f.colperm.cpu().numpy()
     AQJ = A[:, cp][:, ::-1]
-    tol = 1e-10 if mode == "f64_blocked" else (1e-2 if mode == "f32_tf32" else 1e-4)
+    tol = 1e-10 if mode in ("f64_blocked", "f64_ozaki") else (1e-2 if mode == "f32_tf32" else 1e-4)
     assert np.abs(L @ U - AQJ).max() <= tol
 
 
-def test_blocked_f64_matches_plain_pivots():
-    """FP64 blocked reorders roundings only: on a Gaussian matrix it takes the same
-    pivot labels as the plain sweep (no near-ties at this size)."""
+@pytest.mark.parametrize("mode", ["f64_blocked", "f64_ozaki"])
+def test_blocked_f64_matches_plain_pivots(mode):
+    """FP64 blocked reorders roundings only, and the sliced tensor-core update
+    differs from FP64 FMAs by about 2^-47 of a row's largest entry: on a Gaussian
+    matrix both take the plain sweep's pivot labels (no near-ties at this size)."""
     n = 500
     A = workloads.dense_gaussian(n, seed=21)
     fp = api.logdet_factor(torch.from_numpy(A).cuda(), "f64_plain")
-    fb = api.logdet_factor(torch.from_numpy(A).cuda(), "f64_blocked")
+    fb = api.logdet_factor(torch.from_numpy(A).cuda(), mode)
     assert torch.equal(fp.pivot_labels(), fb.pivot_labels())
     assert float(fb.sign) == float(fp.sign)
     assert rel_err(float(fb.logabs), float(fp.logabs)) < 1e-12

@@ -5,7 +5,11 @@ relative to |D| + |A| |B|^T per element (u = unit roundoff of the input format):
   TF32   inputs carry 10 explicit mantissa bits: a few 2^-10, bound 4e-3;
   3xTF32 the dropped lo*lo term and FP32 accumulation: ~2^-20, bound 5e-6;
   BF16x3 hi and lo carry 8 bits each, lo*lo dropped: ~2^-16, bound 1e-4;
-  FP64   K FMAs in FP64: bound 1e-14.
+  FP64   K FMAs in FP64: bound 1e-14;
+  FP64 sliced (Ozaki): each operand row cut at 2^-47 of its largest entry, the
+         slice products exact, one FP64 rounding: per element about
+         2^-47 (max|a| / mean|a| + max|b| / mean|b|) ~ 1e-13 for Gaussian rows,
+         bound 4e-13.
 """
 import numpy as np
 import pytest
@@ -15,11 +19,13 @@ from paper_1811_08057_gb300 import _lib
 
 pytestmark = pytest.mark.gpu
 
-MODES = {"f64_blocked": (1, torch.float64, 1e-14), "f32_tf32": (3, torch.float32, 4e-3),
+MODES = {"f64_blocked": (1, torch.float64, 1e-14), "f64_ozaki": (6, torch.float64, 4e-13),
+         "f32_tf32": (3, torch.float32, 4e-3),
          "f32_3xtf32": (4, torch.float32, 5e-6), "f32_bf16x3": (5, torch.float32, 1e-4)}
 
 SHAPES = [(128, 128, 64), (1, 1, 64), (129, 257, 128), (300, 1000, 128), (1000, 300, 256),
           (37, 5, 64), (2048, 2048, 128)]
+OZAKI_SHAPES = [(3, 70, 1), (200, 129, 33), (130, 65, 200), (64, 64, 300)]  # ragged K, K > 128
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -102,3 +108,59 @@ def test_bf16x3_error_is_the_split():
     assert exact <= 5e-8
     assert general >= 10 * exact
     assert 0.3 * predicted <= general <= 3 * predicted
+
+
+@pytest.mark.parametrize("shape", OZAKI_SHAPES)
+def test_ozaki_any_k(shape):
+    """The sliced FP64 update takes any K (zero-padded chunks of 32, passes of 128)."""
+    M, N, K = shape
+    g = torch.Generator().manual_seed(K + 17)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64)
+    B = torch.randn(N, K, generator=g, dtype=torch.float64)
+    D = torch.randn(M, N, generator=g, dtype=torch.float64)
+    want = D - A @ B.T
+    scale = D.abs() + A.abs() @ B.abs().T
+    Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()  # held: the call only sees raw pointers
+    rc = _lib.ld_rankb_update(6, M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K,
+                              Dd.data_ptr(), N, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    assert ((Dd.cpu() - want).abs() / scale).max().item() <= 4e-13
+
+
+def test_ozaki_exact_on_small_integers():
+    """Integers below 2^7 in magnitude are one slice each and every product and sum
+    is exact: the result equals the FP64 one bit for bit, whatever the row scales
+    (each row multiplied by its own power of two)."""
+    M, N, K = 300, 200, 128
+    g = torch.Generator().manual_seed(3)
+    sa = torch.pow(2.0, torch.randint(-20, 20, (M, 1), generator=g).double())
+    sb = torch.pow(2.0, torch.randint(-20, 20, (N, 1), generator=g).double())
+    A = torch.randint(-127, 128, (M, K), generator=g).double() * sa
+    B = torch.randint(-127, 128, (N, K), generator=g).double() * sb
+    D = torch.randint(-1000, 1000, (M, N), generator=g).double() * (sa @ sb.T)
+    # exact on the host too: element (i, j) is an integer below 2^22 times sa_i sb_j
+    want = D - A @ B.T
+    Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()  # held: the call only sees raw pointers
+    rc = _lib.ld_rankb_update(6, M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K,
+                              Dd.data_ptr(), N, None)
+    assert rc == 0
+    assert torch.equal(Dd.cpu(), want)
+
+
+def test_ozaki_zero_rows_and_nan():
+    M, N, K = 130, 70, 64
+    g = torch.Generator().manual_seed(9)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64)
+    B = torch.randn(N, K, generator=g, dtype=torch.float64)
+    A[5] = 0.0  # a zero multiplier row leaves its D row unchanged
+    A[7, 3] = float("nan")  # a NaN reaches its D row only
+    D = torch.randn(M, N, generator=g, dtype=torch.float64)
+    Ad, Bd, Dd = A.cuda(), B.cuda(), D.cuda()  # held: the call only sees raw pointers
+    rc = _lib.ld_rankb_update(6, M, N, K, Ad.data_ptr(), K, Bd.data_ptr(), K,
+                              Dd.data_ptr(), N, None)
+    assert rc == 0
+    got = Dd.cpu()
+    assert torch.equal(got[5], D[5])
+    assert torch.isnan(got[7]).all()
+    others = [i for i in range(M) if i != 7]
+    assert torch.isfinite(got[others]).all()
