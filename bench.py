@@ -37,9 +37,12 @@ UNIT = "TFLOP/s"
 # nominal dense tensor rates relative to BF16 (TF32 1.1 / BF16 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 DTYPE = {"f64_plain": "f64", "f32_plain": "f32", "f64_blocked": "f64", "f32_tf32": "f32+tf32",
-         "f32_3xtf32": "f32+3xtf32", "f32_bf16x3": "f32+bf16x3"}
-TENSOR_MODES = ("f32_tf32", "f32_3xtf32", "f32_bf16x3")
-ALL_MODES = ["f64_plain", "f32_plain", "f64_blocked", "f32_tf32", "f32_3xtf32", "f32_bf16x3"]
+         "f32_3xtf32": "f32+3xtf32", "f32_bf16x3": "f32+bf16x3", "f64_ozaki": "f64+bf16 slices"}
+TENSOR_MODES = ("f32_tf32", "f32_3xtf32", "f32_bf16x3", "f64_ozaki")
+ALL_MODES = ["f64_plain", "f32_plain", "f64_blocked", "f64_ozaki", "f32_tf32", "f32_3xtf32",
+             "f32_bf16x3"]
+# slice products of the FP64-accurate update per useful product (orders 0..5 of six slices)
+OZAKI_PRODUCTS = 21
 
 # single-matrix workloads: (N, description)
 WORKLOADS = {
@@ -74,6 +77,9 @@ def tensor_peak(mode, peaks=None):
     TF32/BF16 ratio for TF32, divided by the three products of the split kinds."""
     peaks = peaks or read_peaks()
     bf16 = peaks["bf16_tflops_sustained"]
+    if mode == "f64_ozaki":
+        return (bf16 / OZAKI_PRODUCTS,
+                f"BF16 sustained / {OZAKI_PRODUCTS} (slice products per FP64 product)")
     if mode == "f32_bf16x3":
         return bf16 / 3.0, "BF16 sustained / 3 (three products)"
     if mode == "f32_3xtf32":
@@ -309,7 +315,7 @@ def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
            "kernel_ms_per_step": k_ms / steps, "kernel_launches_per_step": k_launches / steps,
            "algorithmic_bytes_per_step": k_bytes / steps,
            "algorithmic_flops_per_step": k_flops / steps}
-    if kernel == "rankb_tc":
+    if kernel in ("rankb_tc", "rankb_ozaki"):
         tr = NCU_TRAFFIC_RATIO.get((kernel, mode))
         if tr and k_launches > 0:
             out["traffic"] = tr["ratio"] * k_bytes / k_launches
@@ -363,9 +369,10 @@ def sweep_roofline(mode, N, ms, shares):
                "traffic": None,
                "traffic_note": "a whole sweep is many launches; the DRAM bytes per launch of its "
                                "dominant kernel are under tensor_update"}
-        if "rankb_tc" in shares:
-            s = shares["rankb_tc"]
-            out["tensor_update"] = make_roofline("rankb_tc", mode, s["bytes"], s["flops"], s["ms"],
+        upd = "rankb_ozaki" if mode == "f64_ozaki" else "rankb_tc"
+        if upd in shares:
+            s = shares[upd]
+            out["tensor_update"] = make_roofline(upd, mode, s["bytes"], s["flops"], s["ms"],
                                                  s["launches"], 1)
     elif mode == "f64_blocked":
         ach = flops(N) / (ms * 1e-3) / 1e12
