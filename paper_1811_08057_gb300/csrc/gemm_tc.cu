@@ -76,7 +76,11 @@ __host__ __device__ constexpr int acc_of(int kc, int nk) {
 // K-chunks [0, nk1) come from the first operand maps, the rest from the second
 // (mAh2 ...): one launch computes D -= A1 B1^T + A2 B2^T with the two products
 // in one accumulation.
-template <int KIND, bool QUAD>
+// PAIR: clusters of two CTAs take column-adjacent tiles (same rows of A): each
+// CTA loads half of every A chunk and multicasts it to both, so a CTA reads 3/4
+// of the operand bytes it would alone; a stage is refilled only once both CTAs'
+// MMAs have released it (the MMA commits arrive on both CTAs' barriers).
+template <int KIND, bool QUAD, bool PAIR>
 __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -103,16 +107,27 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tn = (N + C::BN - 1) / C::BN, tm = (M + C::BM - 1) / C::BM;
-  const int per_z = tn * tm;
+  const int rank = PAIR ? (int)tc::cluster_ctarank() : 0;
+  const int tnu = PAIR ? (tn + 1) / 2 : tn;  // tile columns per row (pairs of them when PAIR)
+  const int per_z = tnu * tm;
   const int total = per_z * batch;
-  const int t_first = blockIdx.x * tpc;
+  const int t_first = (PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * tpc;
   const int ntile = min(tpc, total - t_first);
   const int nk = K / C::BK;
+  // tile it of this CTA: matrix z, rows from m0, columns from n0 (with PAIR the
+  // second CTA of a pair past the last column computes zeros and stores nothing)
+  auto tile_at = [&](int it, int& z, int& m0, int& n0) {
+    const int t = t_first + it;
+    z = t / per_z;
+    const int r = t % per_z;
+    m0 = (r / tnu) * C::BM;
+    n0 = (PAIR ? (r % tnu) * 2 + rank : r % tnu) * C::BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], PAIR ? 2 : 1);
     }
     for (int a = 0; a < 4; ++a) {
       tc::mbar_init(&accf[a], 1);
@@ -134,6 +149,7 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
+  if (PAIR) tc::cluster_sync_all();  // both CTAs' barriers exist before the first multicast
   const uint32_t tmem = *tmem_slot;
   int issued = 0;
 
@@ -142,8 +158,8 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     int g = 0;
     bool ok = true;
     for (int it = 0; it < ntile && ok; ++it) {
-      const int t = t_first + it, z = t / per_z, r = t % per_z;
-      const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+      int z, m0, n0;
+      tile_at(it, z, m0, n0);
       for (int kc = 0; kc < nk; ++kc, ++g) {
         const int s = g % C::STAGES, rnd = g / C::STAGES;
         if (!tc::mbar_wait(&empty[s], (rnd & 1) ^ 1, err)) {
@@ -154,13 +170,20 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
         const bool sec = kc >= nk1;
         const int kx = (sec ? kc - nk1 : kc) * C::BK;
         tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-        tc::tma_load_3d(st, sec ? &mAh2 : &mAh, &full[s], kx, m0, z);
+        if (PAIR) {
+          // this CTA's half of the A rows, into both CTAs of the pair
+          const int ho = rank * (C::A_BYTES / 2), hr = m0 + rank * (C::BM / 2);
+          tc::tma_load_3d_mc(st + ho, sec ? &mAh2 : &mAh, &full[s], kx, hr, z, 3);
+          if (C::NT == 2)
+            tc::tma_load_3d_mc(st + C::A_BYTES + ho, sec ? &mAl2 : &mAl, &full[s], kx, hr, z, 3);
+        } else {
+          tc::tma_load_3d(st, sec ? &mAh2 : &mAh, &full[s], kx, m0, z);
+          if (C::NT == 2) tc::tma_load_3d(st + C::A_BYTES, sec ? &mAl2 : &mAl, &full[s], kx, m0, z);
+        }
         tc::tma_load_3d(st + C::NT * C::A_BYTES, sec ? &mBh2 : &mBh, &full[s], kx, n0, z);
-        if (C::NT == 2) {
-          tc::tma_load_3d(st + C::A_BYTES, sec ? &mAl2 : &mAl, &full[s], kx, m0, z);
+        if (C::NT == 2)
           tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, sec ? &mBl2 : &mBl, &full[s], kx,
                           n0, z);
-        }
         issued = g + 1;
       }
     }
@@ -215,7 +238,10 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
           const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
           // the first chunk of an accumulator overwrites it
           issue_mmas(st, tmem + (uint32_t)(a * C::BN), first ? 0u : 1u);
-          tc::mma_commit(&empty[s]);
+          if (PAIR)
+            tc::mma_commit_mc(&empty[s], 3);  // the stage is shared with the other CTA
+          else
+            tc::mma_commit(&empty[s]);
           if (last) tc::mma_commit(&accf[a]);
         }
       }
@@ -239,7 +265,10 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
           const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
           const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS + (kc % C::NACC) * C::BN);
           issue_mmas(st, d, kc >= C::NACC ? 1u : 0u);
-          tc::mma_commit(&empty[s]);
+          if (PAIR)
+            tc::mma_commit_mc(&empty[s], 3);  // the stage is shared with the other CTA
+          else
+            tc::mma_commit(&empty[s]);
         }
         if (ok) tc::mma_commit(&accf[buf]);
       }
@@ -303,8 +332,8 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     if constexpr (C::QUAD) {
       const int na = nk < 4 ? nk : 4;  // accumulators a tile uses
       for (int it = 0; it < ntile; ++it) {
-        const int t = t_first + it, z = t / per_z, r = t % per_z;
-        const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+        int z, m0, n0;
+        tile_at(it, z, m0, n0);
         float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
                           : D + (int64_t)z * dstride;
         const bool rows_ok = m0 + q * 32 + 32 <= M &&
@@ -371,8 +400,8 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     } else {
       for (int it = 0; it < ntile; ++it) {
         const int buf = it & 1, use = it >> 1;
-        const int t = t_first + it, z = t / per_z, r = t % per_z;
-        const int m0 = (r / tn) * C::BM, n0 = (r % tn) * C::BN;
+        int z, m0, n0;
+        tile_at(it, z, m0, n0);
         float* dz = dptrs ? reinterpret_cast<float*>(static_cast<char*>(dptrs[z]) + doff)
                           : D + (int64_t)z * dstride;
         const bool rows_ok = m0 + q * 32 + 32 <= M &&
@@ -431,6 +460,9 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair leaves while the other may still multicast into it or
+  // arrive on its barriers
+  if (PAIR) tc::cluster_sync_all();
   if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
@@ -561,15 +593,17 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, i
 namespace {
 
 // Maps of one operand pair (hi and, for the split kinds, lo parts).
+// A boxes are a_rows high (all BM rows, or half of them for a CTA pair).
 template <int KIND, bool QUAD>
 bool make_maps(CUtensorMap* mAh, CUtensorMap* mAl, CUtensorMap* mBh, CUtensorMap* mBl,
-               const TcOperand& a, const TcOperand& b, int M, int N, int K, int batch) {
+               const TcOperand& a, const TcOperand& b, int M, int N, int K, int batch,
+               int a_rows) {
   using C = TcCfg<KIND, QUAD>;
-  if (!make_map(mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+  if (!make_map(mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, a_rows) ||
       !make_map(mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
     return false;
   if (C::NT == 2) {
-    if (!make_map(mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+    if (!make_map(mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, a_rows) ||
         !make_map(mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
       return false;
   } else {
@@ -587,10 +621,18 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
                         int* err, cudaStream_t stream, const TcOperand* a2, const TcOperand* b2,
                         int K2) {
   using C = TcCfg<KIND, QUAD>;
+  const int64_t sm = device_sm_count();
+  const int64_t tn = ceil_div(N, C::BN);
+  const int64_t tiles = tn * ceil_div(M, C::BM) * (int64_t)batch;
+  // CTA pairs sharing the A chunks: when a row of tiles has two or more and the
+  // grid is at least two waves
+  const bool pair = tuned_rankb_pair() && tn >= 2 && tiles >= 2 * sm;
+  const int a_rows = pair ? C::BM / 2 : C::BM;
   CUtensorMap mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2;
-  if (!make_maps<KIND, QUAD>(&mAh, &mAl, &mBh, &mBl, a, b, M, N, K, batch)) return LD_ERR_CUDA;
+  if (!make_maps<KIND, QUAD>(&mAh, &mAl, &mBh, &mBl, a, b, M, N, K, batch, a_rows))
+    return LD_ERR_CUDA;
   if (a2 && b2 && K2 > 0) {
-    if (!make_maps<KIND, QUAD>(&mAh2, &mAl2, &mBh2, &mBl2, *a2, *b2, M, N, K2, batch))
+    if (!make_maps<KIND, QUAD>(&mAh2, &mAl2, &mBh2, &mBl2, *a2, *b2, M, N, K2, batch, a_rows))
       return LD_ERR_CUDA;
   } else {
     K2 = 0;
@@ -601,26 +643,48 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
   }
   const int nk1 = K / C::BK;
   K += K2;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[pair]) {
+    if (cudaFuncSetAttribute(pair ? rankb_tc_kernel<KIND, QUAD, true>
+                                  : rankb_tc_kernel<KIND, QUAD, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)C::SMEM) != cudaSuccess)
       return LD_ERR_CUDA;
-    attr_set = true;
+    attr_set[pair] = true;
   }
-  const int64_t tiles = ceil_div(N, C::BN) * ceil_div(M, C::BM) * (int64_t)batch;
   // tiles per CTA: one while the grid is within two waves, else up to four
   // (their epilogues overlap the next tile's loads and MMAs; CTAs stay short so
   // concurrent critical-path kernels still find SMs)
-  const int64_t sm = device_sm_count();
   const int tpc = tiles >= 8 * sm ? 4 : tiles >= 4 * sm ? 2 : 1;
   ProfScope ps("rankb_tc", stream,
                (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),
                (double)batch * 2.0 * M * N * K);
-  rankb_tc_kernel<KIND, QUAD><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM, stream>>>(
-      mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2, nk1, D, ldd, dstride, dptrs, doff, M, N, K,
-      batch, tpc, err);
-  LD_CHECK_LAUNCH();
+  if (!pair) {
+    rankb_tc_kernel<KIND, QUAD, false><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM,
+                                         stream>>>(mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2, nk1,
+                                                   D, ldd, dstride, dptrs, doff, M, N, K, batch,
+                                                   tpc, err);
+    LD_CHECK_LAUNCH();
+    return LD_OK;
+  }
+  // pairs of column-adjacent tiles, one per two-CTA cluster
+  const int64_t pairs = ceil_div(tn, 2) * ceil_div(M, C::BM) * (int64_t)batch;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * ceil_div(pairs, tpc)), 1, 1);
+  cfg.blockDim = dim3(C::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, rankb_tc_kernel<KIND, QUAD, true>, mAh, mAl, mBh, mBl, mAh2, mAl2,
+                         mBh2, mBl2, nk1, D, ldd, dstride, dptrs, doff, M, N, K, batch, tpc,
+                         err) != cudaSuccess)
+    return LD_ERR_CUDA;
   return LD_OK;
 }
 
