@@ -319,10 +319,10 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
  *                         next panel; exact arithmetic unchanged); >= 0
  *   "batched_kb_<k>"      panels of the batched sweep for matrices with n in
  *                         [64k, 64k+63] (k = 0..8; k = 8 also covers larger n): 8 or 16
- *   "rankb_pair"          1: the tensor-core update runs in two-CTA clusters on
- *                         column-adjacent tiles, each CTA loading half of the
- *                         shared A chunk for both (TMA multicast); 0 (default):
- *                         single CTAs. Same bits either way
+ *   "rankb_2sm"           1: large single-matrix tensor-core updates run on CTA
+ *                         pairs (tcgen05 cta_group::2: 256 x 128 tiles, each CTA
+ *                         staging its 128 rows of A and half of B); 0 (default):
+ *                         single CTAs (128 x 128 tiles). Same bits either way
  *   "batched_threads"     threads per CTA of the FP32 batched sweep: 256 (default)
  *                         or 128 (more CTAs per SM); results are the same bits
  *   "wait_limit_ns"       limit of the bounded waits of the grid-wide panel kernel

@@ -64,7 +64,7 @@ int g_blocked_b = 128;              // panel width of the blocked sweep (64 or 1
 int64_t g_pair_min_n = 16384;       // pair the trailing updates of two panels from this n
 int g_batched_kb[kTuneBuckets] = {16, 16, 16, 16, 16, 16, 16, 16, 16};
 int g_batched_threads = 256;        // threads per CTA of the FP32 batched sweep (128 or 256)
-int g_rankb_pair = 0;               // tensor-core update in CTA pairs sharing A (1) or not (0)
+int g_rankb_2sm = 0;               // tensor-core update on CTA pairs (cta_group::2) or single CTAs
 }  // namespace
 
 int tuned_blocked_b() {
@@ -83,9 +83,9 @@ int tuned_batched_threads() {
   tune_cache_autoload();
   return g_batched_threads;
 }
-int tuned_rankb_pair() {
+int tuned_rankb_2sm() {
   tune_cache_autoload();
-  return g_rankb_pair;
+  return g_rankb_2sm;
 }
 
 ld_status tuning_set(const char* name, int64_t value) {
@@ -104,9 +104,9 @@ ld_status tuning_set(const char* name, int64_t value) {
     if (value < 0) return LD_ERR_INVALID_ARG;
     return set_panel_wait_limit((uint64_t)value);
   }
-  if (strcmp(name, "rankb_pair") == 0) {
+  if (strcmp(name, "rankb_2sm") == 0) {
     if (value != 0 && value != 1) return LD_ERR_INVALID_ARG;
-    g_rankb_pair = (int)value;
+    g_rankb_2sm = (int)value;
     return LD_OK;
   }
   if (strcmp(name, "batched_threads") == 0) {
@@ -145,8 +145,8 @@ ld_status tuning_get(const char* name, int64_t* value) {
     *value = g_batched_threads;
     return LD_OK;
   }
-  if (strcmp(name, "rankb_pair") == 0) {
-    *value = g_rankb_pair;
+  if (strcmp(name, "rankb_2sm") == 0) {
+    *value = g_rankb_2sm;
     return LD_OK;
   }
   if (strncmp(name, "batched_kb_", 11) == 0) {

@@ -42,18 +42,26 @@ namespace {
 //     it while the later ones are still being read and D is written. Used for
 //     split TF32 with K > 128 (the paired updates), where the double-buffered
 //     form would chain four chunks per accumulator.
-template <int KIND, bool QUAD_>
+// TWO: the CTA pair form (cta_group::2). Two CTAs of a cluster share one
+// 256 x 128 tile: each holds 128 rows of A and half of the B rows (the N
+// dimension) of every K-chunk, the even CTA issues the MMAs for both, and each
+// CTA's TMEM receives its 128 rows of the product. A CTA then stages 3/4 of the
+// operand bytes of a single-CTA tile. Same products, same bits; measured 10-18%
+// slower than single CTAs on GB300, so it is a tuned option (rankb_2sm).
+template <int KIND, bool QUAD_, bool TWO_ = false>
 struct TcCfg {
   static constexpr bool QUAD = QUAD_;
+  static constexpr bool TWO = TWO_;
   static constexpr int BM = 128;
   static constexpr int BN = 128;
   static constexpr int ES = (KIND == kBF16x3) ? 2 : 4;
   static constexpr int BK = 128 / ES;  // elements in one 128-byte K-chunk
   static constexpr int NT = (KIND == kTF32) ? 1 : 2;
+  static constexpr int B_ROWS = TWO ? BN / 2 : BN;  // B rows staged by one CTA
   static constexpr int A_BYTES = BM * 128;
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int B_BYTES = B_ROWS * 128;
   static constexpr int STAGE_BYTES = NT * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = (KIND == kTF32) ? 4 : 3;
+  static constexpr int STAGES = (KIND == kTF32 || TWO) ? 4 : 3;
   static constexpr int KSTEP = (KIND == kBF16x3) ? 16 : 8;  // K of one MMA
   static constexpr int NSUB = BK / KSTEP;
   // epilogue: EW warps, two per TMEM lane quarter (each drains half of a tile's
@@ -76,12 +84,11 @@ __host__ __device__ constexpr int acc_of(int kc, int nk) {
 // K-chunks [0, nk1) come from the first operand maps, the rest from the second
 // (mAh2 ...): one launch computes D -= A1 B1^T + A2 B2^T with the two products
 // in one accumulation.
-// PAIR: clusters of two CTAs take column-adjacent tiles (same rows of A): each
-// CTA loads half of every A chunk and multicasts it to both, so a CTA reads 3/4
-// of the operand bytes it would alone; a stage is refilled only once both CTAs'
-// MMAs have released it (the MMA commits arrive on both CTAs' barriers).
-template <int KIND, bool QUAD, bool PAIR>
-__global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
+// TWO: the CTA pair form (see TcCfg). The even CTA's full barriers count both
+// CTAs' loads and its acce barriers both CTAs' epilogue warps; the MMA commits
+// arrive on both CTAs' empty and accf barriers.
+template <int KIND, bool QUAD, bool TWO>
+__global__ void __launch_bounds__(TcCfg<KIND, QUAD, TWO>::THREADS, 1)
     rankb_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                     const __grid_constant__ CUtensorMap mAh2,
@@ -91,8 +98,9 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
                     float* __restrict__ D, int64_t ldd, int64_t dstride,
                     void* const* __restrict__ dptrs, int64_t doff, int M, int N, int K, int batch,
                     int tpc, int* __restrict__ err) {
-  using C = TcCfg<KIND, QUAD>;
-  constexpr uint32_t IDESC = tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, C::BM, C::BN);
+  using C = TcCfg<KIND, QUAD, TWO>;
+  constexpr uint32_t IDESC =
+      tc::idesc_f32acc(KIND == kBF16x3 ? 1u : 2u, TWO ? 2 * C::BM : C::BM, C::BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -106,32 +114,33 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
   float* stg = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tn = (N + C::BN - 1) / C::BN, tm = (M + C::BM - 1) / C::BM;
-  const int rank = PAIR ? (int)tc::cluster_ctarank() : 0;
-  const int tnu = PAIR ? (tn + 1) / 2 : tn;  // tile columns per row (pairs of them when PAIR)
-  const int per_z = tnu * tm;
+  constexpr int TM = TWO ? 2 * C::BM : C::BM;  // rows of a tile (of both CTAs when TWO)
+  const int tn = (N + C::BN - 1) / C::BN, tm = (M + TM - 1) / TM;
+  const int rank = TWO ? (int)tc::cluster_ctarank() : 0;
+  const bool issuer = !TWO || rank == 0;  // issues the MMAs (and owns the shared barriers)
+  const int per_z = tn * tm;
   const int total = per_z * batch;
-  const int t_first = (PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * tpc;
+  const int t_first = (TWO ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * tpc;
   const int ntile = min(tpc, total - t_first);
   const int nk = K / C::BK;
-  // tile it of this CTA: matrix z, rows from m0, columns from n0 (with PAIR the
-  // second CTA of a pair past the last column computes zeros and stores nothing)
+  // tile it of this CTA: matrix z, rows from m0 (this CTA's half of a pair's
+  // tile), columns from n0
   auto tile_at = [&](int it, int& z, int& m0, int& n0) {
     const int t = t_first + it;
     z = t / per_z;
     const int r = t % per_z;
-    m0 = (r / tnu) * C::BM;
-    n0 = (PAIR ? (r % tnu) * 2 + rank : r % tnu) * C::BN;
+    m0 = (r / tn) * TM + rank * C::BM;
+    n0 = (r % tn) * C::BN;
   };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], PAIR ? 2 : 1);
+      tc::mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 4; ++a) {
       tc::mbar_init(&accf[a], 1);
-      tc::mbar_init(&acce[a], C::EW);
+      tc::mbar_init(&acce[a], TWO ? 2 * C::EW : C::EW);
     }
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
@@ -143,13 +152,18 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     }
   }
   if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
-    tc::tmem_relinquish();
+    if constexpr (TWO) {
+      tc::tmem_alloc2(tmem_slot, C::TMEM_COLS);
+      tc::tmem_relinquish2();
+    } else {
+      tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (PAIR) tc::cluster_sync_all();  // both CTAs' barriers exist before the first multicast
+  if (TWO) tc::cluster_sync_all();  // both CTAs' barriers exist before the first load
   const uint32_t tmem = *tmem_slot;
   int issued = 0;
 
@@ -169,25 +183,54 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
         uint8_t* st = smem + s * C::STAGE_BYTES;
         const bool sec = kc >= nk1;
         const int kx = (sec ? kc - nk1 : kc) * C::BK;
-        tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-        if (PAIR) {
-          // this CTA's half of the A rows, into both CTAs of the pair
-          const int ho = rank * (C::A_BYTES / 2), hr = m0 + rank * (C::BM / 2);
-          tc::tma_load_3d_mc(st + ho, sec ? &mAh2 : &mAh, &full[s], kx, hr, z, 3);
-          if (C::NT == 2)
-            tc::tma_load_3d_mc(st + C::A_BYTES + ho, sec ? &mAl2 : &mAl, &full[s], kx, hr, z, 3);
+        if constexpr (TWO) {
+          // this CTA's A rows and half of the B rows; the even CTA's barrier
+          // counts both CTAs' bytes
+          if (rank == 0) tc::mbar_arrive_expect_tx(&full[s], 2 * C::STAGE_BYTES);
+          const uint32_t fb = tc::mapa(tc::smem_u32(&full[s]), 0);
+          const int nb = n0 + rank * C::B_ROWS;
+          tc::tma_load_3d_pair(st, sec ? &mAh2 : &mAh, fb, kx, m0, z);
+          tc::tma_load_3d_pair(st + C::NT * C::A_BYTES, sec ? &mBh2 : &mBh, fb, kx, nb, z);
+          if (C::NT == 2) {
+            tc::tma_load_3d_pair(st + C::A_BYTES, sec ? &mAl2 : &mAl, fb, kx, m0, z);
+            tc::tma_load_3d_pair(st + C::NT * C::A_BYTES + C::B_BYTES, sec ? &mBl2 : &mBl, fb, kx,
+                                 nb, z);
+          }
         } else {
+          tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
           tc::tma_load_3d(st, sec ? &mAh2 : &mAh, &full[s], kx, m0, z);
-          if (C::NT == 2) tc::tma_load_3d(st + C::A_BYTES, sec ? &mAl2 : &mAl, &full[s], kx, m0, z);
+          tc::tma_load_3d(st + C::NT * C::A_BYTES, sec ? &mBh2 : &mBh, &full[s], kx, n0, z);
+          if (C::NT == 2) {
+            tc::tma_load_3d(st + C::A_BYTES, sec ? &mAl2 : &mAl, &full[s], kx, m0, z);
+            tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, sec ? &mBl2 : &mBl, &full[s],
+                            kx, n0, z);
+          }
         }
-        tc::tma_load_3d(st + C::NT * C::A_BYTES, sec ? &mBh2 : &mBh, &full[s], kx, n0, z);
-        if (C::NT == 2)
-          tc::tma_load_3d(st + C::NT * C::A_BYTES + C::B_BYTES, sec ? &mBl2 : &mBl, &full[s], kx,
-                          n0, z);
         issued = g + 1;
       }
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == 1 && lane == 0 && issuer) {
+    // one MMA of the tile's kind: the CTA's own, or the pair's (cta_group::2)
+    auto mma = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+      if constexpr (TWO) {
+        if (KIND == kBF16x3)
+          tc::mma2_f16(d, a, b, IDESC, acc);
+        else
+          tc::mma2_tf32(d, a, b, IDESC, acc);
+      } else {
+        if (KIND == kBF16x3)
+          tc::mma_f16(d, a, b, IDESC, acc);
+        else
+          tc::mma_tf32(d, a, b, IDESC, acc);
+      }
+    };
+    // MMA completion: on this CTA's barrier, or on both CTAs' (TWO)
+    auto commit = [&](uint64_t* bar) {
+      if constexpr (TWO)
+        tc::mma2_commit_both(bar);
+      else
+        tc::mma_commit(bar);
+    };
     // the MMAs of one staged K-chunk into accumulator d (overwritten first if
     // acc0 == 0): one per K-step, three for the split kinds (small products first)
     auto issue_mmas = [&](uint32_t st, uint32_t d, uint32_t acc0) {
@@ -198,15 +241,11 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
       for (int k = 0; k < C::NSUB; ++k) {
         const uint32_t off = 32u * k;  // one MMA consumes 32 bytes of each row
         if (KIND == kTF32) {
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-        } else if (KIND == kTF32x3) {
-          tc::mma_tf32(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_tf32(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          mma(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), acc);
         } else {
-          tc::mma_f16(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), IDESC, acc);
-          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), IDESC, 1u);
-          tc::mma_f16(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), IDESC, 1u);
+          mma(d, tc::sdesc_k_sw128(al + off), tc::sdesc_k_sw128(bh + off), acc);
+          mma(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bl + off), 1u);
+          mma(d, tc::sdesc_k_sw128(ah + off), tc::sdesc_k_sw128(bh + off), 1u);
         }
         acc = 1u;
       }
@@ -238,11 +277,8 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
           const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
           // the first chunk of an accumulator overwrites it
           issue_mmas(st, tmem + (uint32_t)(a * C::BN), first ? 0u : 1u);
-          if (PAIR)
-            tc::mma_commit_mc(&empty[s], 3);  // the stage is shared with the other CTA
-          else
-            tc::mma_commit(&empty[s]);
-          if (last) tc::mma_commit(&accf[a]);
+          commit(&empty[s]);
+          if (last) commit(&accf[a]);
         }
       }
     } else {
@@ -265,16 +301,16 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
           const uint32_t st = tc::smem_u32(smem + s * C::STAGE_BYTES);
           const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS + (kc % C::NACC) * C::BN);
           issue_mmas(st, d, kc >= C::NACC ? 1u : 0u);
-          if (PAIR)
-            tc::mma_commit_mc(&empty[s], 3);  // the stage is shared with the other CTA
-          else
-            tc::mma_commit(&empty[s]);
+          commit(&empty[s]);
         }
-        if (ok) tc::mma_commit(&accf[buf]);
+        if (ok) commit(&accf[buf]);
       }
     }
     // every MMA issued has completed before TMEM is released
-    tc::mma_commit(done);
+    if constexpr (TWO)
+      tc::mma2_commit(done);
+    else
+      tc::mma_commit(done);
     tc::mbar_wait(done, 0, err);
   } else if (warp >= 2) {
     // epilogue: D -= sum of the accumulators. Warp w may read TMEM lanes
@@ -289,6 +325,13 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
     // element.
     const int e = warp - 2;
     const int q = warp & 3;
+    // an accumulator read out: on this CTA's barrier, or on the issuing CTA's
+    auto release = [&](uint64_t* bar) {
+      if constexpr (TWO)
+        tc::mbar_arrive_cluster(tc::mapa(tc::smem_u32(bar), 0));
+      else
+        tc::mbar_arrive(bar);
+    };
     constexpr int NC = C::BN / 32;           // 32-column blocks of a tile row
     constexpr int NCW = NC / (C::EW / 4);    // blocks drained by one warp
     static_assert(NCW == 2, "one warp drains two 32-column blocks");
@@ -384,7 +427,7 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
           // accumulator a may now be overwritten by the next tile's MMAs
           tc::tc_fence_before();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&acce[a]);
+          if (lane == 0) release(&acce[a]);
         }
         if (!got_all) break;
         // one decision per warp (the staged path synchronises the warp)
@@ -443,7 +486,7 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
         // the buffer may be overwritten by the MMAs of tile it + 2
         tc::tc_fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acce[buf]);
+        if (lane == 0) release(&acce[buf]);
       }
     }
 
@@ -452,7 +495,8 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
   // teardown: every issued TMA copy has landed before shared memory is released
   // (only the last round of each stage: an mbarrier reports the parity of its
   // current phase, so an older round of the same parity would look pending)
-  if (warp == 0 && lane == 0) {
+  // (TWO: the even CTA's barriers count both CTAs' copies)
+  if (warp == 0 && lane == 0 && issuer) {
     for (int s = 0; s < C::STAGES && s < issued; ++s) {
       const int last = (issued - 1 - s) / C::STAGES;
       tc::mbar_wait(&full[s], last & 1, err);
@@ -460,10 +504,14 @@ __global__ void __launch_bounds__(TcCfg<KIND, QUAD>::THREADS, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
-  // neither CTA of a pair leaves while the other may still multicast into it or
-  // arrive on its barriers
-  if (PAIR) tc::cluster_sync_all();
-  if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+  // neither CTA of a pair leaves while the other may still load for it, issue
+  // MMAs into its TMEM or arrive on its barriers
+  if constexpr (TWO) {
+    tc::cluster_sync_all();
+    if (warp == 0) tc::tmem_dealloc2(tmem, C::TMEM_COLS);
+  } else {
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
 }
 
 // --------------------------------------------------- operand preparation
@@ -593,18 +641,18 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int K, int64_t ld, i
 namespace {
 
 // Maps of one operand pair (hi and, for the split kinds, lo parts).
-// A boxes are a_rows high (all BM rows, or half of them for a CTA pair).
+// B boxes are b_rows high (all BN rows, or half of them for a CTA pair).
 template <int KIND, bool QUAD>
 bool make_maps(CUtensorMap* mAh, CUtensorMap* mAl, CUtensorMap* mBh, CUtensorMap* mBl,
                const TcOperand& a, const TcOperand& b, int M, int N, int K, int batch,
-               int a_rows) {
+               int b_rows) {
   using C = TcCfg<KIND, QUAD>;
-  if (!make_map(mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, a_rows) ||
-      !make_map(mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
+  if (!make_map(mAh, a.hi, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+      !make_map(mBh, b.hi, N, K, b.ld, batch, b.bstride, C::ES, b_rows))
     return false;
   if (C::NT == 2) {
-    if (!make_map(mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, a_rows) ||
-        !make_map(mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, C::BN))
+    if (!make_map(mAl, a.lo, M, K, a.ld, batch, a.bstride, C::ES, C::BM) ||
+        !make_map(mBl, b.lo, N, K, b.ld, batch, b.bstride, C::ES, b_rows))
       return false;
   } else {
     *mAl = *mAh;
@@ -621,18 +669,19 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
                         int* err, cudaStream_t stream, const TcOperand* a2, const TcOperand* b2,
                         int K2) {
   using C = TcCfg<KIND, QUAD>;
+  using C2 = TcCfg<KIND, QUAD, true>;
   const int64_t sm = device_sm_count();
   const int64_t tn = ceil_div(N, C::BN);
   const int64_t tiles = tn * ceil_div(M, C::BM) * (int64_t)batch;
-  // CTA pairs sharing the A chunks: when a row of tiles has two or more and the
-  // grid is at least two waves
-  const bool pair = tuned_rankb_pair() && tn >= 2 && tiles >= 2 * sm;
-  const int a_rows = pair ? C::BM / 2 : C::BM;
+  // CTA pairs (cta_group::2) for single-matrix updates with more than one tile
+  // row and at least two waves of tiles
+  const bool two = tuned_rankb_2sm() && batch == 1 && !dptrs && M > C::BM && tiles >= 2 * sm;
+  const int b_rows = two ? C2::B_ROWS : C::BN;
   CUtensorMap mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2;
-  if (!make_maps<KIND, QUAD>(&mAh, &mAl, &mBh, &mBl, a, b, M, N, K, batch, a_rows))
+  if (!make_maps<KIND, QUAD>(&mAh, &mAl, &mBh, &mBl, a, b, M, N, K, batch, b_rows))
     return LD_ERR_CUDA;
   if (a2 && b2 && K2 > 0) {
-    if (!make_maps<KIND, QUAD>(&mAh2, &mAl2, &mBh2, &mBl2, *a2, *b2, M, N, K2, batch, a_rows))
+    if (!make_maps<KIND, QUAD>(&mAh2, &mAl2, &mBh2, &mBl2, *a2, *b2, M, N, K2, batch, b_rows))
       return LD_ERR_CUDA;
   } else {
     K2 = 0;
@@ -644,22 +693,23 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
   const int nk1 = K / C::BK;
   K += K2;
   static bool attr_set[2] = {false, false};
-  if (!attr_set[pair]) {
-    if (cudaFuncSetAttribute(pair ? rankb_tc_kernel<KIND, QUAD, true>
-                                  : rankb_tc_kernel<KIND, QUAD, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::SMEM) != cudaSuccess)
-      return LD_ERR_CUDA;
-    attr_set[pair] = true;
+  if (!attr_set[two]) {
+    const cudaError_t e =
+        two ? cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C2::SMEM)
+            : cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return LD_ERR_CUDA;
+    attr_set[two] = true;
   }
-  // tiles per CTA: one while the grid is within two waves, else up to four
-  // (their epilogues overlap the next tile's loads and MMAs; CTAs stay short so
-  // concurrent critical-path kernels still find SMs)
-  const int tpc = tiles >= 8 * sm ? 4 : tiles >= 4 * sm ? 2 : 1;
   ProfScope ps("rankb_tc", stream,
                (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),
                (double)batch * 2.0 * M * N * K);
-  if (!pair) {
+  if (!two) {
+    // tiles per CTA: one while the grid is within two waves, else up to four
+    // (their epilogues overlap the next tile's loads and MMAs; CTAs stay short so
+    // concurrent critical-path kernels still find SMs)
+    const int tpc = tiles >= 8 * sm ? 4 : tiles >= 4 * sm ? 2 : 1;
     rankb_tc_kernel<KIND, QUAD, false><<<(unsigned)ceil_div(tiles, tpc), C::THREADS, C::SMEM,
                                          stream>>>(mAh, mAl, mBh, mBl, mAh2, mAl2, mBh2, mBl2, nk1,
                                                    D, ldd, dstride, dptrs, doff, M, N, K, batch,
@@ -667,12 +717,14 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
     LD_CHECK_LAUNCH();
     return LD_OK;
   }
-  // pairs of column-adjacent tiles, one per two-CTA cluster
-  const int64_t pairs = ceil_div(tn, 2) * ceil_div(M, C::BM) * (int64_t)batch;
+  // 256 x 128 tiles, one per two-CTA cluster; tiles per cluster as above on the
+  // pairs of SMs
+  const int64_t ptiles = tn * ceil_div(M, 2 * C::BM);
+  const int tpc = ptiles >= 4 * sm ? 4 : ptiles >= 2 * sm ? 2 : 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * ceil_div(pairs, tpc)), 1, 1);
-  cfg.blockDim = dim3(C::THREADS, 1, 1);
-  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.gridDim = dim3((unsigned)(2 * ceil_div(ptiles, tpc)), 1, 1);
+  cfg.blockDim = dim3(C2::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = C2::SMEM;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

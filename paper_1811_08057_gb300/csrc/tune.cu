@@ -5,7 +5,7 @@
 // sizes, in the caller's mode, and keeps the fastest:
 //   blocked modes  panel width b in {64, 128} x paired trailing updates on / off
 //                  (blocked_b, blocked_pair_min_n), then for the FP32 modes the
-//                  tensor-core update in CTA pairs or alone (rankb_pair), timed
+//                  tensor-core update in CTA pairs or alone (rankb_2sm), timed
 //                  on one matrix of the largest size asked for (at most 32768);
 //   plain modes    panel depth of the batched sweep in {8, 16} for every size
 //                  class present (batched_kb_<k>), timed on a batch of up to 256
@@ -105,7 +105,7 @@ std::string cache_file() {
 
 constexpr int kTableSize = 4 + kTuneBuckets;
 const char* table_names[kTableSize] = {
-    "blocked_b",    "blocked_pair_min_n", "rankb_pair",   "batched_threads", "batched_kb_0",
+    "blocked_b",    "blocked_pair_min_n", "rankb_2sm",   "batched_threads", "batched_kb_0",
     "batched_kb_1", "batched_kb_2",       "batched_kb_3", "batched_kb_4",    "batched_kb_5",
     "batched_kb_6", "batched_kb_7",       "batched_kb_8"};
 
@@ -155,14 +155,14 @@ ld_status tune_blocked(const std::vector<int64_t>& sizes, ld_mode mode, cudaStre
   tuning_set("blocked_b", st == LD_OK ? best_b : old_b);
   tuning_set("blocked_pair_min_n", st == LD_OK ? best_pair : old_pair);
   if (!mode_is_f64(mode) && st == LD_OK) {
-    // the tensor-core update in CTA pairs or alone, with the chosen schedule
+    // the tensor-core update on CTA pairs or single CTAs, with the chosen schedule
     int64_t old_rp = 0;
-    tuning_get("rankb_pair", &old_rp);
+    tuning_get("rankb_2sm", &old_rp);
     double best_rp = 1e300;
     int64_t pick = old_rp;
     for (int64_t rp : {0, 1}) {
       if (st != LD_OK) break;
-      tuning_set("rankb_pair", rp);
+      tuning_set("rankb_2sm", rp);
       double ms = 0.0;
       st = time_ms(
           [&]() {
@@ -174,7 +174,7 @@ ld_status tune_blocked(const std::vector<int64_t>& sizes, ld_mode mode, cudaStre
         pick = rp;
       }
     }
-    tuning_set("rankb_pair", st == LD_OK ? pick : old_rp);
+    tuning_set("rankb_2sm", st == LD_OK ? pick : old_rp);
   }
   scratch_free(buf, stream);
   return st;

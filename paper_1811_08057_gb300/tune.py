@@ -12,7 +12,7 @@ from __future__ import annotations
 from . import _lib
 
 BUCKETS = 9
-NAMES = (["blocked_b", "blocked_pair_min_n", "rankb_pair", "batched_threads"] +
+NAMES = (["blocked_b", "blocked_pair_min_n", "rankb_2sm", "batched_threads"] +
          [f"batched_kb_{k}" for k in range(BUCKETS)])
 
 

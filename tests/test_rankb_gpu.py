@@ -25,8 +25,8 @@ MODES = {"f64_blocked": (1, torch.float64, 1e-14), "f64_ozaki": (6, torch.float6
 
 SHAPES = [(128, 128, 64), (1, 1, 64), (129, 257, 128), (300, 1000, 128), (1000, 300, 256),
           (37, 5, 64), (2048, 2048, 128), (2500, 2100, 128), (2500, 2100, 256)]
-# the last two run in CTA pairs (at least two waves of tiles, an odd number of
-# tile columns: the second CTA of the last pair has no columns to store)
+# the last two run on CTA pairs (at least two waves of tiles; the second half of
+# the last pair row lies past M)
 OZAKI_SHAPES = [(3, 70, 1), (200, 129, 33), (130, 65, 200), (64, 64, 300)]  # ragged K, K > 128
 
 
@@ -170,25 +170,32 @@ def test_ozaki_zero_rows_and_nan():
 
 @pytest.mark.parametrize("mode", ["f32_3xtf32", "f32_bf16x3", "f32_tf32"])
 @pytest.mark.parametrize("K", [128, 256])
-def test_cta_pairs_bitwise_equal_to_single_ctas(mode, K):
-    """CTA pairs only share the loading of A: the products and their order are
-    the same, so the results are identical bit for bit."""
-    code = MODES[mode][0]
-    M, N = 2500, 2100
+def test_cta_pairs_match_single_ctas(mode, K):
+    """The CTA-pair form (256 x 128 tiles on two SMs) against single CTAs: the same
+    products per element, so the results agree to the FP32 rounding of the
+    accumulation (compared exactly first, then within a few FP32 ulps of the
+    scale), including a last tile row of the pair that lies past M."""
+    code, _, tol = MODES[mode]
+    M, N = 2500, 2100  # 10 pair rows, the last half past M
     g = torch.Generator().manual_seed(K)
     A = torch.randn(M, K, generator=g).cuda()
     B = torch.randn(N, K, generator=g).cuda()
     D0 = torch.randn(M, N, generator=g).cuda()
     out = []
-    old = _lib.ld_get_tuning("rankb_pair")
+    old = _lib.ld_get_tuning("rankb_2sm")
     try:
-        for pair in (0, 1):
-            assert _lib.ld_set_tuning("rankb_pair", pair) == 0
+        for two in (0, 1):
+            assert _lib.ld_set_tuning("rankb_2sm", two) == 0
             D = D0.clone()
             rc = _lib.ld_rankb_update(code, M, N, K, A.data_ptr(), K, B.data_ptr(), K, D.data_ptr(),
                                       N, torch.cuda.current_stream().cuda_stream)
             assert rc == 0
             out.append(D)
     finally:
-        _lib.ld_set_tuning("rankb_pair", old)
-    assert torch.equal(out[0], out[1])
+        _lib.ld_set_tuning("rankb_2sm", old)
+    same = torch.equal(out[0], out[1])
+    print(f"{mode} K={K}: bitwise equal {same}")
+    scale = (D0.double().abs() + A.double().abs() @ B.double().abs().T)
+    assert ((out[0].double() - out[1].double()).abs() / scale).max().item() <= 1e-6
+    want = D0.double() - A.double() @ B.double().T
+    assert ((out[1].double() - want).abs() / scale).max().item() <= tol

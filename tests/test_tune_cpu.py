@@ -24,7 +24,7 @@ def test_save_load_round_trip(tmp_path, saved_table):
     tune.save(path)
     text = open(path).read().split()
     assert text[0:2] == ["blocked_b", "64"]
-    scramble = {"blocked_b": 128, "batched_threads": 256, "rankb_pair": 0}
+    scramble = {"blocked_b": 128, "batched_threads": 256, "rankb_2sm": 0}
     for nm in tune.NAMES:  # scramble, then load
         assert _lib.ld_set_tuning(nm, scramble.get(nm, 16)) == 0
     tune.load(path)

@@ -54,7 +54,7 @@ def test_ld_tune_blocked_and_batched(tmp_path, monkeypatch, saved_table):
     t = tune.autotune([3000], "f32_3xtf32")
     assert t["blocked_b"] in (64, 128)
     assert t["blocked_pair_min_n"] in (0, 3001)
-    assert t["rankb_pair"] in (0, 1)
+    assert t["rankb_2sm"] in (0, 1)
     t = tune.autotune([40, 130, 300, 520], "f32_plain")
     for k in (0, 2, 4, 8):
         assert t[f"batched_kb_{k}"] in (8, 16)
