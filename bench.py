@@ -335,18 +335,28 @@ def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
 
 
 def profile_step(_lib, step, dev):
-    """One step with every launch accounted: per-class launches, event time and
-    declared work."""
+    """Per-class launches, event time and declared work of one step. A first
+    pass counts every class's launches and work without events; then each class
+    is timed in a step of its own (events around that class's launches only:
+    with every launch of the concurrent streams bracketed at once, the summed
+    spans came out tens of times longer than the step)."""
     import torch
-    _lib.ld_profile_start(None)
-    step()
-    torch.cuda.synchronize(dev)
-    _lib.ld_profile_stop()
+
+    def one(filt):
+        _lib.ld_profile_start(filt)
+        step()
+        torch.cuda.synchronize(dev)
+        _lib.ld_profile_stop()
+
+    one("\x01")  # a class name no launch has: counts and work only
     shares = {}
     for cls in _lib.ld_profile_classes():
-        nl, tms = _lib.ld_profile_query(cls)
+        nl, _ = _lib.ld_profile_query(cls)
         b, f = _lib.ld_profile_work(cls)
-        shares[cls] = {"launches": nl, "ms": round(tms, 4), "bytes": b, "flops": f}
+        shares[cls] = {"launches": nl, "ms": 0.0, "bytes": b, "flops": f}
+    for cls in shares:
+        one(cls)
+        shares[cls]["ms"] = round(_lib.ld_profile_query(cls)[1], 4)
     tot = sum(v["ms"] for v in shares.values()) or 1.0
     for v in shares.values():
         v["share"] = round(v["ms"] / tot, 4)
