@@ -404,13 +404,17 @@ template <typename T, int OUT>
 ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, int64_t row_begin,
                         int64_t row_end, void* ahi, void* alo, const int* moves, size_t smem,
                         cudaStream_t stream, const BatchSpec& bs) {
+  // the largest panel's need, once: a first call with a narrower panel (b = 64,
+  // or a matrix smaller than one panel) must not cap the later ones
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(trsm_kernel<T, kPanel / 32, OUT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)kPanel * kPanel * sizeof(T))) != cudaSuccess)
       return LD_ERR_CUDA;
     attr = true;
   }
+  if (smem > (size_t)kPanel * kPanel * sizeof(T)) return LD_ERR_UNSUPPORTED;
   const int64_t rows = row_end - row_begin;
   ProfScope ps("trsm", stream, 3.0 * sizeof(T) * (double)rows * bb, (double)rows * bb * bb);
   dim3 grid((unsigned)ceil_div(rows, kTrsmRowsPerCta), 1, (unsigned)bs.count);

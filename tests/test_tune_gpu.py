@@ -89,3 +89,29 @@ def test_blocked_panel_width_64_parity(saved_table):
         Ad, sgn, la, perm = workloads.dyadic_lu(300, seed=1)
         f = api.logdet_factor(torch.from_numpy(Ad).cuda(), "f32_3xtf32")
         assert np.array_equal(f.pivot_labels().cpu().numpy(), perm)
+
+
+def test_fresh_process_narrow_panels_first():
+    """In a fresh process, sweeps with narrow panels first (b = 64, then a matrix
+    smaller than one panel) must not cap the shared memory of later full panels;
+    ld_tune itself times b = 64 before b = 128."""
+    code = (
+        "import json, torch, numpy as np; "
+        "from paper_1811_08057_gb300 import api, _lib, tune; "
+        "assert _lib.ld_set_tuning('blocked_b', 64) == 0; "
+        "g = torch.Generator().manual_seed(1); "
+        "A = (torch.randn(700, 700, generator=g, dtype=torch.float64) / 700 ** 0.5 + 2 * torch.eye(700, dtype=torch.float64)).cuda(); "
+        "s1, l1 = api.logdet(A, 'f32_3xtf32'); "
+        "assert _lib.ld_set_tuning('blocked_b', 128) == 0; "
+        "s2, l2 = api.logdet(A, 'f32_3xtf32'); "
+        "s3, l3 = api.logdet(A[:100, :100].contiguous(), 'f64_blocked'); "
+        "s4, l4 = api.logdet(A, 'f64_blocked'); "
+        "t = tune.autotune([2000], 'f32_3xtf32'); "
+        "print(json.dumps([float(l1), float(l2), float(l3), float(l4), float(s1 * s2 * s3 * s4)]))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    import json
+    l1, l2, l3, l4, s = json.loads(out.stdout.strip().splitlines()[-1])
+    assert s == 1.0
+    assert abs(l1 - l4) <= 1e-5 * max(1.0, abs(l4)) and abs(l2 - l4) <= 1e-5 * max(1.0, abs(l4))
