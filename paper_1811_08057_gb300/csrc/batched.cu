@@ -762,12 +762,13 @@ ld_status run_batched_bt(const void* const* A_ptrs, ld_dtype a_dtype, const int6
   const size_t smem = (size_t)kKB * batched_pitch(n_max) * sizeof(T) + (size_t)n_max * 4 +
                       4 * kKB * 4 + 16 + (size_t)BT * kKB * sizeof(T) + 64;
   if (smem > 200 * 1024) return LD_ERR_UNSUPPORTED;
-  static size_t smem_set = 0;  // one per instantiation
-  if (smem > 48 * 1024 && smem_set < smem) {
+  static size_t smem_set[kMaxDevices] = {};  // per instantiation and device
+  const int dv = current_device_index();
+  if (smem > 48 * 1024 && smem_set[dv] < smem) {
     if (cudaFuncSetAttribute(batched_kernel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return LD_ERR_CUDA;
-    smem_set = smem;
+    smem_set[dv] = smem;
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T, BT>, BT, smem) !=

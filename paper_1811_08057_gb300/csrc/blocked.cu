@@ -406,13 +406,14 @@ ld_status launch_trsm_t(T* F, int64_t ldf, int64_t s0, int64_t bb, int64_t m0, i
                         cudaStream_t stream, const BatchSpec& bs) {
   // the largest panel's need, once: a first call with a narrower panel (b = 64,
   // or a matrix smaller than one panel) must not cap the later ones
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[kMaxDevices] = {};
+  const int dv = current_device_index();
+  if (!attr[dv]) {
     if (cudaFuncSetAttribute(trsm_kernel<T, kPanel / 32, OUT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)kPanel * kPanel * sizeof(T))) != cudaSuccess)
       return LD_ERR_CUDA;
-    attr = true;
+    attr[dv] = true;
   }
   if (smem > (size_t)kPanel * kPanel * sizeof(T)) return LD_ERR_UNSUPPORTED;
   const int64_t rows = row_end - row_begin;

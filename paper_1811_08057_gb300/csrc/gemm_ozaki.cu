@@ -373,12 +373,13 @@ ld_status ozaki_gemm(const OzOperand& a, const OzOperand& b, int64_t M, int64_t 
   if (!make_slice_map(&mA, a.sl, (int)M, (int)a.kp, a.cap * a.kp, kOzBM) ||
       !make_slice_map(&mB, b.sl, (int)N, (int)b.kp, b.cap * b.kp, kOzBN))
     return LD_ERR_CUDA;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = current_device_index();
+  if (!attr_set[dv]) {
     if (cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kOzSmem) != cudaSuccess)
       return LD_ERR_CUDA;
-    attr_set = true;
+    attr_set[dv] = true;
   }
   const int64_t tiles = ceil_div(N, kOzBN) * ceil_div(M, kOzBM);
   const int64_t sm = device_sm_count();

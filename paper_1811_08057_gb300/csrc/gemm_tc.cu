@@ -692,15 +692,16 @@ ld_status launch_tc_cfg(const TcOperand& a, const TcOperand& b, int M, int N, in
   }
   const int nk1 = K / C::BK;
   K += K2;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[two]) {
+  static bool attr_set[kMaxDevices][2] = {};
+  const int dv = current_device_index();
+  if (!attr_set[dv][two]) {
     const cudaError_t e =
         two ? cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD, true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C2::SMEM)
             : cudaFuncSetAttribute(rankb_tc_kernel<KIND, QUAD, false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return LD_ERR_CUDA;
-    attr_set[two] = true;
+    attr_set[dv][two] = true;
   }
   ProfScope ps("rankb_tc", stream,
                (double)batch * (8.0 * M * N + (double)(M + N) * K * C::ES * C::NT),

@@ -646,13 +646,13 @@ ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row
                           : (size_t)bb * W * sizeof(T) + kPanelMax * sizeof(T) + (size_t)W * 4 + 16;
   if (smem > 227 * 1024) return LD_ERR_UNSUPPORTED;
   const void* fn = F32 ? (const void*)panel_kernel_f32 : (const void*)panel_kernel<T>;
-  static size_t smem_set[2] = {0, 0};
-  const int ti = F32 ? 0 : 1;
-  if (smem > 48 * 1024 && smem_set[ti] < smem) {
+  static size_t smem_set[kMaxDevices][2] = {};
+  const int ti = F32 ? 0 : 1, dv = current_device_index();
+  if (smem > 48 * 1024 && smem_set[dv][ti] < smem) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)std::max<size_t>(smem, 200 * 1024)) != cudaSuccess)
       return LD_ERR_CUDA;
-    smem_set[ti] = std::max<size_t>(smem, 200 * 1024);
+    smem_set[dv][ti] = std::max<size_t>(smem, 200 * 1024);
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPT, smem) != cudaSuccess ||

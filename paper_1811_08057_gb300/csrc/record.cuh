@@ -20,6 +20,17 @@ inline bool mode_is_blocked(ld_mode mode) {
   return mode == LD_F64_BLOCKED || mode == LD_F64_OZAKI || mode == LD_F32_TF32 ||
          mode == LD_F32_3XTF32 || mode == LD_F32_BF16X3;
 }
+// Index of the current device for once-per-device set-up (function attributes
+// are set per device); 0 if it cannot be had.
+constexpr int kMaxDevices = 64;
+inline int current_device_index() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  return d;
+}
 inline int64_t leading_dim(int64_t n) { return (int64_t)align_up((size_t)(n > 0 ? n : 1), 32); }
 
 // Header at offset 0 of a factor record (256 bytes reserved).
