@@ -337,9 +337,11 @@ def make_roofline(kernel, mode, k_bytes, k_flops, k_ms, k_launches, steps):
 def profile_step(_lib, step, dev):
     """Per-class launches, event time and declared work of one step. A first
     pass counts every class's launches and work without events; then each class
-    is timed in a step of its own (events around that class's launches only:
-    with every launch of the concurrent streams bracketed at once, the summed
-    spans came out tens of times longer than the step)."""
+    is timed in steps of its own, once pipelined and once with the sweep on one
+    stream (events around that class's launches only: with every launch of the
+    concurrent streams bracketed at once, the summed spans came out tens of times
+    longer than the step). The dominant kernel's own roofline is timed again over
+    the timed region."""
     import torch
 
     def one(filt):
@@ -354,12 +356,24 @@ def profile_step(_lib, step, dev):
         nl, _ = _lib.ld_profile_query(cls)
         b, f = _lib.ld_profile_work(cls)
         shares[cls] = {"launches": nl, "ms": 0.0, "bytes": b, "flops": f}
+    # "ms": the class's summed spans in the pipelined sweep (what the rooflines
+    # use); "ms_serial" and "share": the same with the sweep on one stream, one
+    # launch after another, comparable with a profiler's launch list (on the
+    # overlapped low-priority streams a span also counts the wait for SMs)
     for cls in shares:
         one(cls)
         shares[cls]["ms"] = round(_lib.ld_profile_query(cls)[1], 4)
-    tot = sum(v["ms"] for v in shares.values()) or 1.0
+    old = _lib.ld_get_tuning("sweep_pipeline")
+    _lib.ld_set_tuning("sweep_pipeline", 0)
+    try:
+        for cls in shares:
+            one(cls)
+            shares[cls]["ms_serial"] = round(_lib.ld_profile_query(cls)[1], 4)
+    finally:
+        _lib.ld_set_tuning("sweep_pipeline", old)
+    tot = sum(v["ms_serial"] for v in shares.values()) or 1.0
     for v in shares.values():
-        v["share"] = round(v["ms"] / tot, 4)
+        v["share"] = round(v["ms_serial"] / tot, 4)
     return shares
 
 
@@ -399,7 +413,8 @@ def sweep_roofline(mode, N, ms, shares):
             out = upd
         else:
             out["rank1_update"] = upd
-    out["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
+    out["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"],
+                                "ms_serial": v.get("ms_serial"), "share": v["share"]}
                             for k, v in shares.items()}
     return out
 
@@ -707,7 +722,8 @@ def other_workload_line(workload, pk, _lib, dev, warmup, steps, world=1, full=Fa
             roof["tensor_update"] = make_roofline("rankb_tc", "f32_3xtf32", s["bytes"], s["flops"],
                                                   s["ms"], s["launches"], 1)
     if roof is not None:
-        roof["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
+        roof["kernel_shares"] = {k: {"launches": v["launches"], "ms": v["ms"],
+                                     "ms_serial": v.get("ms_serial"), "share": v["share"]}
                                  for k, v in shares.items()}
     value = world * units / (ms * 1e-3)
     res = {"value": value, "unit": unit, "ms_per_step": ms, "tflops": flop / (ms * 1e-3) / 1e12,

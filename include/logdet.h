@@ -325,6 +325,11 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
  *                         single CTAs (128 x 128 tiles). Same bits either way
  *   "batched_threads"     threads per CTA of the FP32 batched sweep: 256 (default)
  *                         or 128 (more CTAs per SM); results are the same bits
+ *   "sweep_pipeline"      1 (default): the blocked sweeps run the panel chain and the
+ *                         trailing updates on prioritised streams that overlap;
+ *                         0: everything on the caller's stream, one launch after
+ *                         another (for measuring each kernel alone). Same results.
+ *                         Not in the tune file
  *   "wait_limit_ns"       limit of the bounded waits of the grid-wide panel kernel
  *                         (LD_F64_BLOCKED's panels) on the current device, >= 0,
  *                         default 1e9; a wait that runs out flags the sweep, its

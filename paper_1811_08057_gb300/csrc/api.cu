@@ -64,6 +64,7 @@ int g_blocked_b = 128;              // panel width of the blocked sweep (64 or 1
 int64_t g_pair_min_n = 16384;       // pair the trailing updates of two panels from this n
 int g_batched_kb[kTuneBuckets] = {16, 16, 16, 16, 16, 16, 16, 16, 16};
 int g_batched_threads = 256;        // threads per CTA of the FP32 batched sweep (128 or 256)
+int g_sweep_pipeline = 1;           // blocked sweeps on the prioritised streams (1) or one (0)
 int g_rankb_2sm = 0;               // tensor-core update on CTA pairs (cta_group::2) or single CTAs
 }  // namespace
 
@@ -83,6 +84,7 @@ int tuned_batched_threads() {
   tune_cache_autoload();
   return g_batched_threads;
 }
+int tuned_sweep_pipeline() { return g_sweep_pipeline; }
 int tuned_rankb_2sm() {
   tune_cache_autoload();
   return g_rankb_2sm;
@@ -98,6 +100,11 @@ ld_status tuning_set(const char* name, int64_t value) {
   if (strcmp(name, "blocked_pair_min_n") == 0) {
     if (value < 0) return LD_ERR_INVALID_ARG;
     g_pair_min_n = value;
+    return LD_OK;
+  }
+  if (strcmp(name, "sweep_pipeline") == 0) {
+    if (value != 0 && value != 1) return LD_ERR_INVALID_ARG;
+    g_sweep_pipeline = (int)value;
     return LD_OK;
   }
   if (strcmp(name, "wait_limit_ns") == 0) {
@@ -133,6 +140,10 @@ ld_status tuning_get(const char* name, int64_t* value) {
   }
   if (strcmp(name, "blocked_pair_min_n") == 0) {
     *value = g_pair_min_n;
+    return LD_OK;
+  }
+  if (strcmp(name, "sweep_pipeline") == 0) {
+    *value = g_sweep_pipeline;
     return LD_OK;
   }
   if (strcmp(name, "wait_limit_ns") == 0) {

@@ -595,7 +595,7 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
   // they cannot be had)
   SweepStreams ss;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, hi->lo, lo->hi, hi->aux
-  bool piped = sweep_streams(&ss);
+  bool piped = tuned_sweep_pipeline() && sweep_streams(&ss);
   for (int i = 0; i < 4 && piped; ++i)
     if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();

@@ -127,6 +127,7 @@ int64_t tuned_pair_min_n();
 const int* tuned_batched_kb();
 int tuned_batched_threads();
 int tuned_rankb_2sm();
+int tuned_sweep_pipeline();
 // The table itself (no cache loading): set / get one entry by name.
 ld_status tuning_set(const char* name, int64_t value);
 ld_status tuning_get(const char* name, int64_t* value);
