@@ -115,3 +115,24 @@ def test_fresh_process_narrow_panels_first():
     l1, l2, l3, l4, s = json.loads(out.stdout.strip().splitlines()[-1])
     assert s == 1.0
     assert abs(l1 - l4) <= 1e-5 * max(1.0, abs(l4)) and abs(l2 - l4) <= 1e-5 * max(1.0, abs(l4))
+
+
+@pytest.mark.parametrize("mode,pair_min", [("f32_3xtf32", 0), ("f32_3xtf32", 10 ** 9),
+                                           ("f64_ozaki", 10 ** 9), ("f64_blocked", 10 ** 9)])
+def test_one_stream_sweep_same_bits(saved_table, mode, pair_min):
+    """sweep_pipeline = 0 runs the blocked sweep on the caller's stream only: the
+    same operations per element, so the same bits as the pipelined sweep."""
+    n = 1500
+    A = torch.from_numpy(workloads.dense_gaussian(n, seed=8, var=1.0 / n)).cuda()
+    assert _lib.ld_set_tuning("blocked_pair_min_n", pair_min) == 0
+    out = []
+    try:
+        for pipe in (1, 0):
+            assert _lib.ld_set_tuning("sweep_pipeline", pipe) == 0
+            f = api.logdet_factor(A, mode)
+            torch.cuda.synchronize()
+            out.append((float(f.sign), float(f.logabs), f.pivot_labels().clone()))
+    finally:
+        _lib.ld_set_tuning("sweep_pipeline", 1)
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert torch.equal(out[0][2], out[1][2])
