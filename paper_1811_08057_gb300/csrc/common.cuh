@@ -37,6 +37,19 @@ struct Cand {
   int pad;
 };
 
+// a / b rounded to nearest (binary32) from y = RN(1/b), by Markstein's
+// correction step (P. Markstein, "Computation of elementary functions on the
+// IBM RISC System/6000 processor", IBM J. Res. Develop. 34(1), 1990): q0 =
+// RN(a y), the remainder r = a - b q0 exactly (one FMA), then RN(q0 + r y). With
+// y the correctly rounded reciprocal this is the correctly rounded quotient for
+// normal results (a subnormal quotient may differ in its last place). One
+// reciprocal per divisor, then three operations per quotient: for many
+// quotients with one divisor (a pivot row).
+__device__ __forceinline__ float div_by_recip(float a, float b, float y) {
+  const float q0 = a * y;
+  return fmaf(fmaf(-b, q0, a), y, q0);
+}
+
 __device__ __forceinline__ void cand_init(Cand& c) {
   c.absv = -1.0;
   c.v = 0.0;

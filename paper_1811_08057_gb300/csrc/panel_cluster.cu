@@ -18,9 +18,9 @@
 //     an mbarrier (a fixed number per pivot);
 //   - once its bytes are in, every warp reduces the CL candidates from its own
 //     shared memory (identical everywhere), and each thread, on its own positions,
-//     exchanges columns l and m-1 (Sec. 2.4), divides row t by p (IEEE FP32
-//     divide, Eq. (3)) and applies the rank-1 update to the inner block's later
-//     rows (Eq. (2)).
+//     exchanges columns l and m-1 (Sec. 2.4), divides row t by p (the correctly
+//     rounded FP32 quotient, Eq. (3)) and applies the rank-1 update to the
+//     inner block's later rows (Eq. (2)).
 // Buffers and mbarriers alternate by pivot parity: a CTA pushes pivot t+2 only
 // after every CTA's pivot t+1 data reached it, which each CTA sends only after it
 // has finished with pivot t. A wait that runs out of time (it never should)
@@ -286,16 +286,18 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
           }
         }
       }
-      // row t factored (IEEE FP32 divide: the FP64 quotient rounded to FP32),
-      // then the rank-1 update of the block's later rows, position by position
+      // row t factored (the correctly rounded FP32 quotient, from one correctly
+      // rounded reciprocal of the pivot per thread: div_by_recip), then the
+      // rank-1 update of the block's later rows, position by position
       const int jend = min(w_own, m - 1 - j_lo);
+      const float pinv = __frcp_rn(pf);
       float rk[K];
       bool act[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
         act[k] = j < jend;
-        rk[k] = act[k] ? __fdiv_rn((j == jl) ? lc[t] : cur[k], pf) : 0.f;
+        rk[k] = act[k] ? div_by_recip((j == jl) ? lc[t] : cur[k], pf, pinv) : 0.f;
       }
       switch (t) {
 #define LD_BLOCK_UPDATE_CASE(T) \
