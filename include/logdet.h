@@ -331,7 +331,9 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
  *                         another (for measuring each kernel alone). Same results.
  *                         Not in the tune file
  *   "wait_limit_ns"       limit of the bounded waits of the grid-wide panel kernel
- *                         (LD_F64_BLOCKED's panels) on the current device, >= 0,
+ *                         (the FP64 blocked modes' panels wider than 16 x 1024
+ *                         positions, or every panel with LD_PANEL=grid in the
+ *                         environment) on the current device, >= 0,
  *                         default 1e9; a wait that runs out flags the sweep, its
  *                         results become NaN and the call returns LD_ERR_TIMEOUT
  *                         (when it reads its results back). Not in the tune file.

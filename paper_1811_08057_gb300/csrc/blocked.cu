@@ -613,7 +613,9 @@ ld_status run_blocked_t(const void* A, ld_dtype a_dtype, int64_t lda, const Reco
     const int* moves = reinterpret_cast<const int*>(cl_scratch[par]);  // the panel's move list
     bool used_cluster = false;
     ld_status pst = LD_ERR_UNSUPPORTED;
-    if (!per_pivot && !no_cluster && sizeof(T) == 4) {
+    // the cluster panel (FP32; FP64 while the active width allows its register
+    // block, else the grid-wide panel below)
+    if (!per_pivot && !no_cluster) {
       pst = launch_panel_cluster(r, s0, bb, keep ? 0 : s0, cl_scratch[par], aux != hi, hi);
       used_cluster = (pst == LD_OK);
       if (used_cluster && aux != hi) {

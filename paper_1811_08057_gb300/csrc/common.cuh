@@ -257,6 +257,69 @@ __device__ __forceinline__ int kc_warp_best(KCand& c) {
   return src;
 }
 
+// Keyed FP64 candidate: the ordering of KCand on 64-bit keys (the bit pattern of
+// |v| plus one, 0 = no candidate, a NaN the largest key; equal keys go to the
+// smaller original label), reduced over a warp in two 32-bit redux.sync steps.
+constexpr unsigned long long kKeyNaN64 = ~0ull;
+
+struct KCandD {
+  unsigned long long key;
+  int label;
+  unsigned ps;
+};
+
+__device__ __forceinline__ void kc_init(KCandD& c) {
+  c.key = 0ull;
+  c.label = 0x7fffffff;
+  c.ps = 0u;
+}
+
+__device__ __forceinline__ void kc_offer(KCandD& c, double v, int label, int pos) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long ab = bits & 0x7fffffffffffffffull;
+  const unsigned long long key = (ab > 0x7ff0000000000000ull) ? kKeyNaN64 : ab + 1ull;
+  if (key > c.key || (key == c.key && label < c.label)) {
+    c.key = key;
+    c.label = label;
+    c.ps = (unsigned)pos | ((unsigned)(bits >> 32) & 0x80000000u);
+  }
+}
+
+__device__ __forceinline__ int kc_pos(const KCandD& c) { return (int)(c.ps & 0x7fffffffu); }
+__device__ __forceinline__ double kc_value(const KCandD& c) {
+  return __longlong_as_double(
+      (long long)((c.key - 1ull) | ((unsigned long long)(c.ps & 0x80000000u) << 32)));
+}
+
+// As kc_warp_best for KCand.
+__device__ __forceinline__ int kc_warp_best(KCandD& c) {
+  const unsigned hi = (unsigned)(c.key >> 32), lo = (unsigned)c.key;
+  const unsigned hmax = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned lmax = __reduce_max_sync(0xffffffffu, hi == hmax ? lo : 0u);
+  const unsigned long long kmax = ((unsigned long long)hmax << 32) | lmax;
+  unsigned won = __ballot_sync(0xffffffffu, c.key == kmax);
+  if ((won & (won - 1u)) != 0u && kmax != 0ull && kmax != kKeyNaN64) {
+    const unsigned lab = (c.key == kmax) ? (unsigned)c.label : 0xffffffffu;
+    const unsigned lmin = __reduce_min_sync(0xffffffffu, lab);
+    won = __ballot_sync(0xffffffffu, c.key == kmax && (unsigned)c.label == lmin);
+  }
+  const int src = __ffs(won) - 1;
+  c.key = kmax;
+  c.label = __shfl_sync(0xffffffffu, c.label, src);
+  c.ps = __shfl_sync(0xffffffffu, c.ps, src);
+  return src;
+}
+
+// Whether a reduced candidate exists, is NaN, or is a usable (nonzero, non-NaN) pivot.
+__device__ __forceinline__ bool kc_has(const KCand& c) { return c.key != 0u; }
+__device__ __forceinline__ bool kc_has(const KCandD& c) { return c.key != 0ull; }
+__device__ __forceinline__ bool kc_isnan(const KCand& c) { return c.key == kKeyNaN; }
+__device__ __forceinline__ bool kc_isnan(const KCandD& c) { return c.key == kKeyNaN64; }
+__device__ __forceinline__ bool kc_ok(const KCand& c) { return c.key != kKeyNaN && c.key > 1u; }
+__device__ __forceinline__ bool kc_ok(const KCandD& c) {
+  return c.key != kKeyNaN64 && c.key > 1ull;
+}
+
 // Sign and Neumaier log-sum of pivots [first, first + count) of a panel whose
 // first step has `m0` active columns, in pivot order: warp-parallel logs, one
 // lane adds them in order (the same operations as a per-pivot accumulation).

@@ -1,4 +1,7 @@
-// Panel of the blocked sweep on one thread-block cluster (FP32 storage).
+// Panel of the blocked sweep on one thread-block cluster (FP32 storage, or FP64
+// storage with at most 4 positions per thread: the FP64 blocked modes take the
+// grid-wide panel of panel.cu for wider panels). The FP64 form makes the same
+// steps with an FP64 keyed candidate, 8-byte pushes and the IEEE FP64 divide.
 //
 // A cluster of CL CTAs (one GPC) runs all b pivot steps of the panel at rows
 // s0 .. s0+b-1 (m0 active columns). CTA c owns column positions [c*W, (c+1)*W)
@@ -54,7 +57,7 @@ constexpr int kBMax = 128;  // largest panel
 constexpr int kCLMax = 16;  // largest cluster
 
 struct ClusterArgs {
-  float* F;
+  void* F;          // float or double, the record's storage type
   int64_t ldf;
   int n, s0, bb, m0;
   int W;            // columns per CTA
@@ -76,35 +79,89 @@ struct ClusterArgs {
 // Row t of the block factored (x[t] = r) and the rank-1 update of its later
 // rows with multipliers pcv, for pivot row T of the block: static register
 // indices (one instance per T, picked by a switch on the uniform pivot index).
-template <int T, int K>
-__device__ __forceinline__ void block_update(float (&x)[kKI][K], float (&cur)[K],
-                                             const float (&r)[K], const float (&pcv)[kKI], int kb,
-                                             const bool (&act)[K]) {
+template <int T, int K, typename E>
+__device__ __forceinline__ void block_update(E (&x)[kKI][K], E (&cur)[K], const E (&r)[K],
+                                             const E (&pcv)[kKI], int kb, const bool (&act)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (act[k]) {
       x[T][k] = r[k];
 #pragma unroll
       for (int i = T + 1; i < kKI; ++i)
-        if (i < kb) x[i][k] = fmaf(-pcv[i], r[k], x[i][k]);
+        if (i < kb) x[i][k] = fma_t(-pcv[i], r[k], x[i][k]);
       if (T + 1 < kKI) cur[k] = x[T + 1 < kKI ? T + 1 : T][k];
     }
   }
 }
 
+// Element-type specifics of the panel: the keyed candidate, its 16-byte push
+// form, one value pushed with st.async, row t's quotient and four consecutive
+// multipliers of a row below.
+template <typename E> struct PanelKey;
+template <> struct PanelKey<float> { using type = KCand; };
+template <> struct PanelKey<double> { using type = KCandD; };
+
+__device__ __forceinline__ uint4 kc_pack(const KCand& c) {
+  return make_uint4(c.key, (unsigned)c.label, c.ps, 0u);
+}
+__device__ __forceinline__ uint4 kc_pack(const KCandD& c) {
+  return make_uint4((unsigned)c.key, (unsigned)(c.key >> 32), (unsigned)c.label, c.ps);
+}
+__device__ __forceinline__ void kc_unpack(const uint4& q, KCand& c) {
+  c.key = q.x;
+  c.label = (int)q.y;
+  c.ps = q.z;
+}
+__device__ __forceinline__ void kc_unpack(const uint4& q, KCandD& c) {
+  c.key = ((unsigned long long)q.y << 32) | q.x;
+  c.label = (int)q.z;
+  c.ps = q.w;
+}
+__device__ __forceinline__ void push_value(uint32_t raddr, float v, uint32_t rbar) {
+  tc::st_async_b32(raddr, __float_as_uint(v), rbar);
+}
+__device__ __forceinline__ void push_value(uint32_t raddr, double v, uint32_t rbar) {
+  tc::st_async_b64(raddr, (uint64_t)__double_as_longlong(v), rbar);
+}
+// FP32: the correctly rounded quotient from one correctly rounded reciprocal per
+// thread (div_by_recip, the IEEE quotient's bits); FP64: the IEEE divide.
+__device__ __forceinline__ float pivot_recip(float p) { return __frcp_rn(p); }
+__device__ __forceinline__ double pivot_recip(double) { return 0.0; }
+__device__ __forceinline__ float quotient(float v, float p, float pinv) {
+  return div_by_recip(v, p, pinv);
+}
+__device__ __forceinline__ double quotient(double v, double p, double) { return v / p; }
+__device__ __forceinline__ void load4(const float* p, float (&c)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  c[0] = q.x;
+  c[1] = q.y;
+  c[2] = q.z;
+  c[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&c)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p);
+  const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+  c[0] = q0.x;
+  c[1] = q0.y;
+  c[2] = q1.x;
+  c[3] = q1.y;
+}
+
+// E: storage type (float, or double for the FP64 modes, K <= 4).
 // K: positions per thread (W <= K * kCT). The thread's values of the inner
 // block live in registers: x[i][k] = row i at position c*W + tid + k*kCT.
-template <int K>
+template <typename E, int K>
 __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
+  using Key = typename PanelKey<E>::type;
   // rows per register tile of the rows-below update (deeper while registers allow)
-  constexpr int kRU = K <= 2 ? 16 : 8;
+  constexpr int kRU = sizeof(E) == 4 ? (K <= 2 ? 16 : 8) : (K <= 1 ? 8 : 4);
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
   if (a.recs) {
     const int z = blockIdx.x / CL;
     char* b = static_cast<char*>(a.recs[z]);
-    a.F = reinterpret_cast<float*>(b + a.ro.F);
+    a.F = b + a.ro.F;
     a.colperm = reinterpret_cast<int*>(b + a.ro.colperm);
     a.pivpos = reinterpret_cast<int*>(b + a.ro.pivpos);
     a.pivval = reinterpret_cast<double*>(b + a.ro.pivval);
@@ -118,22 +175,22 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   const int w_own = max(0, j_hi - j_lo);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* U = reinterpret_cast<float*>(smem_raw);          // kKI x kKI (block's U)
-  float* Cm = U + kKI * kKI;                              // kBMax x kKI multipliers below
+  E* U = reinterpret_cast<E*>(smem_raw);                  // kKI x kKI (block's U)
+  E* Cm = U + kKI * kKI;                                  // kBMax x kKI multipliers below
   int* lab = reinterpret_cast<int*>(Cm + kBMax * kKI);    // W labels
   __shared__ __align__(16) uint4 pslot[2][kCLMax];  // candidates pushed by every CTA
-  __shared__ float pcand[2][kCLMax][kKI];           // their columns
-  __shared__ float plast[2][kKI];                   // boundary column, pushed by its owner
+  __shared__ E pcand[2][kCLMax][kKI];               // their columns
+  __shared__ E plast[2][kKI];                       // boundary column, pushed by its owner
   __shared__ int plastlab[2];
   __shared__ __align__(8) uint64_t xbar[2];         // bytes received per pivot parity
-  __shared__ KCand wred[2][kCT / 32];
-  __shared__ float wcol[2][kCT / 32][kKI];          // each warp's candidate column
-  __shared__ float lcol[2][kKI];                    // this CTA's boundary column, if owned
+  __shared__ Key wred[2][kCT / 32];
+  __shared__ E wcol[2][kCT / 32][kKI];              // each warp's candidate column
+  __shared__ E lcol[2][kKI];                        // this CTA's boundary column, if owned
   __shared__ int s_nmoved;
   __shared__ int s_swap[kKI];
   __shared__ int mv_dst[2 * kKI], mv_src[2 * kKI];
 
-  float* F = a.F;
+  E* F = static_cast<E*>(a.F);
   for (int j = tid; j < w_own; j += kCT) lab[j] = a.colperm[j_lo + j];
   if (c == 0 && tid == 0) a.dlist[0] = 0;  // read only after the cluster barriers below
   double sign = 0.0, sum = 0.0, comp = 0.0;
@@ -150,10 +207,11 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
   }
   // bytes every CTA receives per pivot: CL candidates with their columns, the
   // boundary column and its label
-  const uint32_t xbytes = (uint32_t)CL * (16u + 4u * kKI) + 4u * kKI + 4u;
+  constexpr uint32_t es = (uint32_t)sizeof(E);
+  const uint32_t xbytes = (uint32_t)CL * (16u + es * kKI) + es * kKI + 4u;
   cluster.sync();  // every mbarrier initialised before the first push
 
-  float x[kKI][K];  // the inner block at the own positions
+  E x[kKI][K];  // the inner block at the own positions
   for (int q0 = 0; q0 < bb; q0 += kKI) {
     const int kb = min(kKI, bb - q0);
     const int mq = m0 - q0;  // active columns at the start of this inner block
@@ -165,9 +223,9 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
-        x[i][k] = (!bad && i < kb && j < w_own) ? __ldcg(F + (row0 + i) * a.ldf + j_lo + j) : 0.f;
+        x[i][k] = (!bad && i < kb && j < w_own) ? __ldcg(F + (row0 + i) * a.ldf + j_lo + j) : E(0);
       }
-    float cur[K];  // the current pivot row at the own positions
+    E cur[K];  // the current pivot row at the own positions
 #pragma unroll
     for (int k = 0; k < K; ++k) cur[k] = x[0][k];
     for (int t = 0; t < kb && !bad; ++t) {
@@ -175,7 +233,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       const int gi = q0 + t;  // pivot index in the panel
       const int par = gi & 1;
       // candidate of row t over the own positions < m, then warp and CTA best
-      KCand cd;
+      Key cd;
       kc_init(cd);
       const int w_act = min(w_own, m - j_lo);
 #pragma unroll
@@ -187,7 +245,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // the warp's candidate column and (its owner) the boundary column, staged
       // for the push
       const int jc = kc_pos(cd) - j_lo;
-      if (lane == src && cd.key != 0u) {
+      if (lane == src && kc_has(cd)) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
           if (tid + k * kCT == jc)
@@ -205,7 +263,7 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       }
       if (lane == 0) wred[par][warp] = cd;
       __syncthreads();
-      KCand cb;
+      Key cb;
       if (lane < kCT / 32)
         cb = wred[par][lane];
       else
@@ -217,15 +275,15 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       for (int e = tid; e < CL * kKI; e += kCT) {
         const int d = e / kKI, i = e % kKI;
         const uint32_t rbar = tc::mapa(bar_l, d);
-        const float cv = (i < kb && cb.key != 0u) ? wcol[par][wb][i] : 0.f;
-        tc::st_async_b32(tc::mapa(tc::smem_u32(&pcand[par][c][i]), d), __float_as_uint(cv), rbar);
+        const E cv = (i < kb && kc_has(cb)) ? wcol[par][wb][i] : E(0);
+        push_value(tc::mapa(tc::smem_u32(&pcand[par][c][i]), d), cv, rbar);
         if (own_last) {
-          const float lv = (i < kb) ? lcol[par][i] : 0.f;
-          tc::st_async_b32(tc::mapa(tc::smem_u32(&plast[par][i]), d), __float_as_uint(lv), rbar);
+          const E lv = (i < kb) ? lcol[par][i] : E(0);
+          push_value(tc::mapa(tc::smem_u32(&plast[par][i]), d), lv, rbar);
         }
         if (i == 0) {
-          tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), cb.key, (uint32_t)cb.label,
-                          cb.ps, 0u, rbar);
+          const uint4 pk = kc_pack(cb);
+          tc::st_async_v4(tc::mapa(tc::smem_u32(&pslot[par][c]), d), pk.x, pk.y, pk.z, pk.w, rbar);
           if (own_last)
             tc::st_async_b32(tc::mapa(tc::smem_u32(&plastlab[par]), d), (uint32_t)lab[jm], rbar);
         }
@@ -236,33 +294,28 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
         bad = 1;
         break;
       }
-      KCand g;
-      if (lane < CL) {
-        const uint4 q = pslot[par][lane];
-        g.key = q.x;
-        g.label = (int)q.y;
-        g.ps = q.z;
-      } else {
+      Key g;
+      if (lane < CL)
+        kc_unpack(pslot[par][lane], g);
+      else
         kc_init(g);
-      }
       const int wc = kc_warp_best(g);  // the winning CTA (identical in every warp)
-      const bool ok = g.key != kKeyNaN && g.key > 1u;
-      if (!ok) {
-        if (c == 0 && tid == 0) atomicOr(&a.st->flags, g.key == kKeyNaN ? kFlagNaN : kFlagSingular);
+      if (!kc_ok(g)) {
+        if (c == 0 && tid == 0) atomicOr(&a.st->flags, kc_isnan(g) ? kFlagNaN : kFlagSingular);
         bad = 1;
         break;
       }
       const int l = kc_pos(g);
-      const float pf = kc_value(g);
+      const E pf = kc_value(g);
       if (tid == 0) s_swap[t] = l;
       if (c == 0 && tid == 0) {  // the sign and the log-sum are accumulated after the panel
         a.pivpos[row0 + t] = l;
         a.pivval[row0 + t] = (double)pf;
       }
-      const float* pc = pcand[par][wc];  // pivot column: the multipliers of the block's rows
-      const float* lc = plast[par];      // boundary column
+      const E* pc = pcand[par][wc];  // pivot column: the multipliers of the block's rows
+      const E* lc = plast[par];      // boundary column
       const int jl = l - j_lo;
-      float pcv[kKI];
+      E pcv[kKI];
 #pragma unroll
       for (int i = 0; i < kKI; ++i) pcv[i] = pc[i];
       const bool own_l = jl >= 0 && jl < w_own && jl % kCT == tid;
@@ -290,14 +343,14 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // rounded reciprocal of the pivot per thread: div_by_recip), then the
       // rank-1 update of the block's later rows, position by position
       const int jend = min(w_own, m - 1 - j_lo);
-      const float pinv = __frcp_rn(pf);
-      float rk[K];
+      const E pinv = pivot_recip(pf);
+      E rk[K];
       bool act[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int j = tid + k * kCT;
         act[k] = j < jend;
-        rk[k] = act[k] ? div_by_recip((j == jl) ? lc[t] : cur[k], pf, pinv) : 0.f;
+        rk[k] = act[k] ? quotient((j == jl) ? lc[t] : cur[k], pf, pinv) : E(0);
       }
       switch (t) {
 #define LD_BLOCK_UPDATE_CASE(T) \
@@ -372,8 +425,8 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
     const int nmoved = bad ? 0 : s_nmoved;
     // finished inner blocks above keep the record layout: the exchanges reach them
     for (int r = c * (kCT / 32) + warp; r < q0 && !bad; r += CL * (kCT / 32)) {
-      float* row = F + (int64_t)(a.s0 + r) * a.ldf;
-      float mvv = 0.f;
+      E* row = F + (int64_t)(a.s0 + r) * a.ldf;
+      E mvv = E(0);
       if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
       __syncwarp();
       if (lane < nmoved) row[mv_dst[lane]] = mvv;
@@ -382,21 +435,21 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // U block of the inner block: U[t'][t] = factored row t' at position mq-1-t
       for (int e = tid; e < kb * kb && !bad; e += kCT) {
         const int tp = e / kb, t = e % kb;
-        U[tp * kKI + t] = (tp < t) ? __ldcg(F + (row0 + tp) * a.ldf + (mq - 1 - t)) : 0.f;
+        U[tp * kKI + t] = (tp < t) ? __ldcg(F + (row0 + tp) * a.ldf + (mq - 1 - t)) : E(0);
       }
       __syncthreads();
       // (a) moves and multipliers of the panel rows below: one warp per row
       for (int r = c * (kCT / 32) + warp; r < rows_below && !bad; r += CL * (kCT / 32)) {
-        float* row = F + (row0 + kb + r) * a.ldf;
-        float mvv = 0.f;
+        E* row = F + (row0 + kb + r) * a.ldf;
+        E mvv = E(0);
         if (lane < nmoved) mvv = __ldcg(row + mv_src[lane]);
         __syncwarp();
         if (lane < nmoved) row[mv_dst[lane]] = mvv;
         __syncwarp();
-        float x = (lane < kb) ? __ldcg(row + (mq - 1 - lane)) : 0.f;
+        E x = (lane < kb) ? __ldcg(row + (mq - 1 - lane)) : E(0);
         for (int t = 0; t < kb; ++t) {
-          const float ct = __shfl_sync(0xffffffffu, x, t);
-          if (lane > t && lane < kb) x = fmaf(-ct, U[t * kKI + lane], x);
+          const E ct = __shfl_sync(0xffffffffu, x, t);
+          if (lane > t && lane < kb) x = fma_t(-ct, U[t * kKI + lane], x);
         }
         if (lane < kb) {
           row[mq - 1 - lane] = x;  // multipliers (L) of this block
@@ -407,30 +460,29 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
       // (b) the block's rank-1 updates on the own positions, in pivot order:
       // register tiles of kRU rows x 2 positions, their loads in flight together
       const int wq = bad ? 0 : max(0, min(j_hi, mq - kb) - j_lo);
-      const float4* Cm4 = reinterpret_cast<const float4*>(Cm);
-      float* base = F + (row0 + kb) * a.ldf + j_lo;
+      E* base = F + (row0 + kb) * a.ldf + j_lo;
 #pragma unroll
       for (int kp = 0; kp < K; kp += 2) {
         const int j0 = tid + kp * kCT;
         if (j0 >= wq) break;
         const int j1 = j0 + kCT;
         const bool has1 = kp + 1 < K && j1 < wq;
-        float s0v[kKI], s1v[kKI];
+        E s0v[kKI], s1v[kKI];
 #pragma unroll
         for (int t = 0; t < kKI; ++t) {
           s0v[t] = x[t][kp];
-          s1v[t] = has1 ? x[t][kp + 1 < K ? kp + 1 : kp] : 0.f;
+          s1v[t] = has1 ? x[t][kp + 1 < K ? kp + 1 : kp] : E(0);
         }
         // the next chunk's loads are issued before this chunk's FMAs
-        float n0[kRU], n1[kRU];
+        E n0[kRU], n1[kRU];
 #pragma unroll
         for (int u = 0; u < kRU; ++u) {
           const bool in = u < rows_below;
-          n0[u] = in ? __ldcg(base + (int64_t)u * a.ldf + j0) : 0.f;
-          n1[u] = (in && has1) ? __ldcg(base + (int64_t)u * a.ldf + j1) : 0.f;
+          n0[u] = in ? __ldcg(base + (int64_t)u * a.ldf + j0) : E(0);
+          n1[u] = (in && has1) ? __ldcg(base + (int64_t)u * a.ldf + j1) : E(0);
         }
         for (int r0 = 0; r0 < rows_below; r0 += kRU) {
-          float v0[kRU], v1[kRU];
+          E v0[kRU], v1[kRU];
 #pragma unroll
           for (int u = 0; u < kRU; ++u) {
             v0[u] = n0[u];
@@ -440,22 +492,22 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
 #pragma unroll
             for (int u = 0; u < kRU; ++u) {
               const bool in = r0 + kRU + u < rows_below;
-              n0[u] = in ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j0) : 0.f;
-              n1[u] = (in && has1) ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j1) : 0.f;
+              n0[u] = in ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j0) : E(0);
+              n1[u] = (in && has1) ? __ldcg(base + (int64_t)(r0 + kRU + u) * a.ldf + j1) : E(0);
             }
           }
 #pragma unroll
           for (int u = 0; u < kRU; ++u) {
 #pragma unroll
             for (int t4 = 0; t4 < kKI / 4; ++t4) {
-              const float4 c4 = Cm4[(r0 + u) * (kKI / 4) + t4];
-              const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+              E cc[4];
+              load4(Cm + (r0 + u) * kKI + 4 * t4, cc);
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const int t = 4 * t4 + q;
                 if (t < kb) {
-                  v0[u] = fmaf(-cc[q], s0v[t], v0[u]);
-                  v1[u] = fmaf(-cc[q], s1v[t], v1[u]);
+                  v0[u] = fma_t(-cc[q], s0v[t], v0[u]);
+                  v1[u] = fma_t(-cc[q], s1v[t], v1[u]);
                 }
               }
             }
@@ -518,19 +570,20 @@ __global__ void __launch_bounds__(kCT, 1) panel_cluster_kernel(ClusterArgs a) {
 }
 
 // Applies the panel's composed column moves to rows [r0, r1) (one warp per row).
-__global__ void apply_moves_kernel(float* __restrict__ F, int64_t ldf, int r0, int r1,
+template <typename E>
+__global__ void apply_moves_kernel(E* __restrict__ F, int64_t ldf, int r0, int r1,
                                    const int* __restrict__ moves) {
   const int nm = moves[0];
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = r0 + wid; r < r1; r += nw) {
-    float* row = F + (int64_t)r * ldf;
-    float v[8];
+    E* row = F + (int64_t)r * ldf;
+    E v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = lane + 32 * q;
-      v[q] = (k < nm) ? row[moves[2 + 2 * k]] : 0.f;
+      v[q] = (k < nm) ? row[moves[2 + 2 * k]] : E(0);
     }
     __syncwarp();
 #pragma unroll
@@ -582,9 +635,15 @@ size_t panel_cluster_scratch_bytes() {
 // leaves the panel's sign and log-sum to launch_panel_logsum. LD_ERR_UNSUPPORTED
 // when the cluster cannot be formed or the slice does not fit (the caller falls
 // back).
-ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
-                               void* scratch, bool defer_logsum, cudaStream_t stream) {
-  if (mode_is_f64(r.mode) || bb > kBMax) return LD_ERR_UNSUPPORTED;
+namespace {
+
+template <typename E>
+ld_status launch_panel_cluster_t(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
+                                 void* scratch, bool defer_logsum, cudaStream_t stream) {
+  // positions per thread: up to 8 in FP32; in FP64 up to 4 (a 16 x 4 double
+  // inner block in registers), beyond which the caller takes the grid panel
+  constexpr int kMaxK = sizeof(E) == 4 ? 8 : 4;
+  if (bb > kBMax) return LD_ERR_UNSUPPORTED;
   const int64_t m0 = r.n - s0;
   static int cl_ok = -1;  // cluster size that formed before (16 or 8), 0 = none
   if (cl_ok == 0) return LD_ERR_UNSUPPORTED;
@@ -596,13 +655,14 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     // a multiple of 32 positions per CTA: every warp's row segment is one
     // 128-byte line (ldf is a multiple of 32); 2% faster than ceil(m0 / CL)
     const int64_t W = align_up((size_t)ceil_div(m0, CL), 32);
-    const size_t smem = kKI * kKI * 4 + (size_t)kBMax * kKI * 4 + (size_t)W * 4;
-    if (smem > 200 * 1024 || W > 8 * kCT) continue;
+    const size_t smem =
+        ((size_t)kKI * kKI + (size_t)kBMax * kKI) * sizeof(E) + (size_t)W * 4;
+    if (smem > 200 * 1024 || W > kMaxK * kCT) continue;
     const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
-    void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<1>
-                                : K == 2 ? panel_cluster_kernel<2>
-                                : K == 4 ? panel_cluster_kernel<4>
-                                         : panel_cluster_kernel<8>;
+    void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<E, 1>
+                                : K == 2 ? panel_cluster_kernel<E, 2>
+                                : K == 4 ? panel_cluster_kernel<E, 4>
+                                         : panel_cluster_kernel<E, sizeof(E) == 4 ? 8 : 4>;
     tried = true;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (CL > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -628,12 +688,13 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
     int* moves = static_cast<int*>(scratch);  // at offset 0: see the header
     int* dlist = reinterpret_cast<int*>(static_cast<char*>(scratch) +
                                         align_up((1 + 4 * kBMax) * 4, kAlign));
-    ClusterArgs a{static_cast<float*>(r.F), r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
+    ClusterArgs a{r.F, r.ldf, (int)r.n, (int)s0, (int)bb, (int)m0, (int)W,
                   r.colperm, r.pivpos, r.pivval, r.state, moves, dlist, defer_logsum ? 0 : 1,
                   nullptr, RecOffsets{}, 0};
     cudaError_t e;
     {
-      ProfScope ps("panel", stream, 4.0 * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
+      ProfScope ps("panel", stream,
+                   (double)sizeof(E) * (2.0 * bb * m0 + 2.0 * bb * bb * m0 / kKI),
                    (double)bb * bb * m0);
       e = cudaLaunchKernelEx(&cfg, kern, a);
     }
@@ -648,14 +709,24 @@ ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t 
       const int rows = (int)(s0 - swap_row_begin);
       const int grid = (int)std::min<int64_t>(ceil_div(rows, 8), device_sm_count() * 4);
       ProfScope ps("apply_moves", stream, 8.0 * rows * 2 * bb, 0.0);
-      apply_moves_kernel<<<grid, 256, 0, stream>>>(static_cast<float*>(r.F), r.ldf,
-                                                   (int)swap_row_begin, (int)s0, moves);
+      apply_moves_kernel<E><<<grid, 256, 0, stream>>>(static_cast<E*>(r.F), r.ldf,
+                                                      (int)swap_row_begin, (int)s0, moves);
       if (cudaGetLastError() != cudaSuccess) return LD_ERR_CUDA;
     }
     return LD_OK;
   }
   if (tried && cl_ok < 0) cl_ok = 0;  // no cluster of 16 or 8 forms on this device
   return LD_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+ld_status launch_panel_cluster(const Record& r, int64_t s0, int64_t bb, int64_t swap_row_begin,
+                               void* scratch, bool defer_logsum, cudaStream_t stream) {
+  if (mode_is_f64(r.mode))
+    return launch_panel_cluster_t<double>(r, s0, bb, swap_row_begin, scratch, defer_logsum,
+                                          stream);
+  return launch_panel_cluster_t<float>(r, s0, bb, swap_row_begin, scratch, defer_logsum, stream);
 }
 
 // Batched form: one single-CTA cluster per matrix, `count` matrices of size n
@@ -670,10 +741,10 @@ ld_status launch_panel_cluster_batched(void* const* recs, const RecOffsets& ro, 
   const int64_t W = m0;
   if (W > 8 * kCT) return LD_ERR_UNSUPPORTED;
   const int K = W <= kCT ? 1 : W <= 2 * kCT ? 2 : W <= 4 * kCT ? 4 : 8;
-  void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<1>
-                              : K == 2 ? panel_cluster_kernel<2>
-                              : K == 4 ? panel_cluster_kernel<4>
-                                       : panel_cluster_kernel<8>;
+  void (*kern)(ClusterArgs) = K == 1   ? panel_cluster_kernel<float, 1>
+                              : K == 2 ? panel_cluster_kernel<float, 2>
+                              : K == 4 ? panel_cluster_kernel<float, 4>
+                                       : panel_cluster_kernel<float, 8>;
   const size_t smem = kKI * kKI * 4 + (size_t)kBMax * kKI * 4 + (size_t)W * 4;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaLaunchConfig_t cfg = {};
@@ -716,7 +787,7 @@ ld_status launch_apply_moves(float* F, int64_t ldf, int64_t r0, int64_t r1, cons
   const int rows = (int)(r1 - r0);
   const int grid = (int)std::min<int64_t>(ceil_div(rows, 8), device_sm_count() * 4);
   ProfScope ps("apply_moves", stream, 8.0 * rows * 2 * kBMax, 0.0);
-  apply_moves_kernel<<<grid, 256, 0, stream>>>(F, ldf, (int)r0, (int)r1, moves);
+  apply_moves_kernel<float><<<grid, 256, 0, stream>>>(F, ldf, (int)r0, (int)r1, moves);
   return cudaGetLastError() == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }
 

@@ -226,7 +226,8 @@ ld_status launch_panel(const Record& r, int64_t s0, int64_t bb, int64_t swap_row
 ld_status set_panel_wait_limit(uint64_t ns);
 ld_status get_panel_wait_limit(uint64_t* ns);
 
-// ---- cluster panel kernel (panel_cluster.cu), FP32 storage ----
+// ---- cluster panel kernel (panel_cluster.cu): FP32 storage, and FP64 while
+// the active width is at most 4 x 256 positions per CTA ----
 // Scratch of one launch; it starts with the panel's composed column moves for
 // the rows outside the panel: int count, then count (dst, src) position pairs.
 size_t panel_cluster_scratch_bytes();

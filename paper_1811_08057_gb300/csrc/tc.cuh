@@ -92,6 +92,12 @@ __device__ __forceinline__ void st_async_b32(uint32_t raddr, uint32_t v, uint32_
                "r"(v), "r"(rbar)
                : "memory");
 }
+__device__ __forceinline__ void st_async_b64(uint32_t raddr, uint64_t v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(
+                   raddr),
+               "l"(v), "r"(rbar)
+               : "memory");
+}
 __device__ __forceinline__ void st_async_v4(uint32_t raddr, uint32_t a, uint32_t b, uint32_t c,
                                             uint32_t d, uint32_t rbar) {
   asm volatile(

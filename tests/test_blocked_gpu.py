@@ -158,15 +158,20 @@ def test_panel_kernel_matches_per_pivot_launches(mode, monkeypatch):
     assert torch.equal(fa.F[:, :n], fb.F[:, :n])  # columns past n are padding
 
 
-@pytest.mark.parametrize("n", [300, 700, 2100])
-def test_cluster_panel_matches_grid_panel(n, monkeypatch):
+@pytest.mark.parametrize("mode,n", [("f32_3xtf32", 300), ("f32_3xtf32", 700),
+                                    ("f32_3xtf32", 2100), ("f64_blocked", 300),
+                                    ("f64_blocked", 2100), ("f64_ozaki", 700),
+                                    ("f64_ozaki", 9000)])
+def test_cluster_panel_matches_grid_panel(mode, n, monkeypatch):
     """The cluster panel (inner blocks of 16 in distributed shared memory, deferred
     in-order updates) and the grid-wide panel kernel perform the same operations:
-    identical pivots, factors and log|det| bits (FP32 storage)."""
+    identical pivots, factors and log|det| bits, in FP32 storage and in FP64 (at
+    n = 9000 the FP64 panel holds 4, 2 and 1 positions per thread as the active
+    width shrinks)."""
     A = torch.from_numpy(workloads.dense_gaussian(n, seed=n, var=1.0 / n)).cuda()
-    fa = api.logdet_factor(A, "f32_3xtf32")
+    fa = api.logdet_factor(A, mode)
     monkeypatch.setenv("LD_PANEL", "grid")
-    fb = api.logdet_factor(A, "f32_3xtf32")
+    fb = api.logdet_factor(A, mode)
     monkeypatch.setenv("LD_PANEL", "")
     assert torch.equal(fa.pivot_labels(), fb.pivot_labels())
     assert torch.equal(fa.pivval, fb.pivval)
@@ -174,5 +179,5 @@ def test_cluster_panel_matches_grid_panel(n, monkeypatch):
     assert torch.equal(fa.F[:, :n], fb.F[:, :n])
     # the non-factor path (trailing rows get the composed moves in the multiplier
     # kernel) gives the same result
-    s, l = api.logdet(A, "f32_3xtf32")
+    s, l = api.logdet(A, mode)
     assert float(l) == float(fa.logabs) and float(s) == float(fa.sign)

@@ -216,12 +216,14 @@ def test_f64_config_8000_full_sequence():
     assert rel_err(float(f.logabs), ref.logabs) <= F64_TOL
 
 
-def test_wait_limit_runs_out_and_context_stays_usable():
+def test_wait_limit_runs_out_and_context_stays_usable(monkeypatch):
     """A bounded device wait that runs out: with the grid panel's wait limit at 0
-    (LD_F64_BLOCKED's panels poll global-memory tags), the tag barrier gives up,
-    the sweep is flagged, the results are NaN and the call reports LD_ERR_TIMEOUT.
-    The context stays usable: with the limit restored the same call succeeds."""
+    (the grid-wide panel, selected here with LD_PANEL=grid, polls global-memory
+    tags), the tag barrier gives up, the sweep is flagged, the results are NaN and
+    the call reports LD_ERR_TIMEOUT. The context stays usable: with the limit
+    restored the same call succeeds."""
     import ctypes
+    monkeypatch.setenv("LD_PANEL", "grid")
     n = 1000  # 16 panel CTAs and 1000 tag barriers: some wait outlasts a timer tick
     A = workloads.dense_gaussian(n, seed=61)
     At = torch.from_numpy(A).cuda()
