@@ -287,7 +287,7 @@ def run_reference(args):
 # class, workload). Reported only for the workload it was taken on.
 NCU_TRAFFIC = {
     ("batched", "batched4096"): {
-        "bytes": 11445127936 + 11567744256,
+        "bytes": 11523763712 + 11589309952,
         "launch": "the whole batch (one launch per step)",
         "summary": "profiles/batched_kernel_spd4096.md"},
 }
@@ -299,7 +299,7 @@ NCU_TRAFFIC = {
 # class, mode).
 NCU_TRAFFIC_RATIO = {
     ("rankb_tc", "f32_3xtf32"): {
-        "ratio": (31064824064 + 20301085184) / 50070683648.0,
+        "ratio": (30959057152 + 20334375680) / 50070683648.0,
         "captured": "all 314 launches of one N=16384 SPD sweep (3xTF32)",
         "summary": "profiles/rankb_tc_traffic_3xtf32_spd16384.md"},
 }
