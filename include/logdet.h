@@ -311,6 +311,56 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
                             double* sign, double* logabs);
 
 /*
+ * ld_logdet_sparse - sign and log|det| of an n x n sparse matrix in CSR form. The
+ * paper names sparse matrices as future work without a method; this entry point
+ * condenses only the diagonal blocks of A's block triangular form (Duff and
+ * Reid's reduction): a complete transversal sigma (a stored entry a(i, sigma(i))
+ * in every row; without one the matrix is structurally singular and det A = 0),
+ * the strongly connected components of the graph of A P_sigma, then
+ * det A = sgn(sigma) * prod_k det(block_k), every block condensed on the GPU
+ * (Eqs. (2)-(3)): blocks of up to 512, and of up to 1024 (with a blocked mode:
+ * when there are at least half as many of those as SMs), in persistent batched
+ * launches with the plain sweep in the mode's precision (LD_F64_PLAIN for the
+ * FP64 modes, LD_F32_PLAIN for the FP32 ones); the other blocks with ld_logdet
+ * in `mode`. With every diagonal entry stored, the transversal is the identity;
+ * otherwise it is a maximum matching (Hopcroft-Karp phases after a greedy
+ * start; about 1 s on the host for a scrambled structure with 1e6 entries).
+ *   row_ptr  n + 1 int64 offsets (row_ptr[0] = 0, nondecreasing; nnz = row_ptr[n])
+ *   col_idx  nnz int64 column indices, distinct within a row, in [0, n)
+ *   vals     nnz values of type v_dtype, in col_idx order
+ *            (each array host or device memory, detected with
+ *            cudaPointerGetAttributes; the structure is analysed on the host)
+ *   sign, logabs  as ld_logdet (host or device pointers)
+ * Stored zeros count as entries of the structure. Entries outside the diagonal
+ * blocks do not enter the result (as in exact arithmetic), so a NaN or an
+ * infinity there is not propagated. The call waits for `stream` before it
+ * returns (the structure analysis needs the host).
+ * Errors: LD_ERR_INVALID_ARG for n < 0, NULL arrays (n > 0), a malformed
+ * structure (row_ptr[0] != 0, decreasing offsets, a column out of range or
+ * repeated in a row) or an unknown enum; LD_ERR_ALLOC / LD_ERR_CUDA as named;
+ * the errors of ld_logdet / ld_logdet_batched for the blocks.
+ */
+ld_status ld_logdet_sparse(const int64_t* row_ptr, const int64_t* col_idx, const void* vals,
+                           ld_dtype v_dtype, int64_t n, ld_mode mode, void* stream, double* sign,
+                           double* logabs);
+
+/*
+ * ld_sparse_blocks - the structure analysis of ld_logdet_sparse on its own (host
+ * only, no GPU work). All pointers are host memory.
+ *   col_of_row    out, n entries: the transversal sigma (a(i, sigma(i)) stored)
+ *   block_of_row  out, n entries: the strongly connected component of row i in
+ *                 the graph with an edge i -> k for every stored a(i, sigma(k));
+ *                 components are numbered in an order in which every edge goes
+ *                 from a higher or equal number to a lower or equal one
+ *   nblocks       out: the number of components; -1 when no complete
+ *                 transversal exists (structurally singular; the outputs are then
+ *                 unspecified)
+ * Errors: LD_ERR_INVALID_ARG as for ld_logdet_sparse.
+ */
+ld_status ld_sparse_blocks(const int64_t* row_ptr, const int64_t* col_idx, int64_t n,
+                           int64_t* col_of_row, int64_t* block_of_row, int64_t* nblocks);
+
+/*
  * Tuning table used by the launchers (process-wide; ld_tune sets it from timings):
  *   "blocked_b"           panel width b of the blocked sweep: 64 or 128 (default 128)
  *   "blocked_pair_min_n"  from this n on (default 16384), FP32 blocked sweeps pair

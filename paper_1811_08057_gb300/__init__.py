@@ -34,7 +34,9 @@ from .api import (  # noqa: F401
     logdet,
     logdet_batched,
     logdet_factor,
+    logdet_sparse,
     logdet_variant,
     logdet_variant_factor,
     parse_factors,
+    sparse_blocks,
 )

@@ -63,6 +63,8 @@ SIGNATURES = {
     "ld_logdet_backward_batched": ([_vp, _i64, _i64, _int, _vp, _vp, _i64, _vp], _int),
     "ld_rankb_update": ([_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _int),
     "ld_logdet_noalloc": ([_vp, _int, _i64, _i64, _vp, _pd, _pd], _int),
+    "ld_logdet_sparse": ([_vp, _vp, _vp, _int, _i64, _int, _vp, _pd, _pd], _int),
+    "ld_sparse_blocks": ([_vp, _vp, _i64, _vp, _vp, _vp], _int),
     "ld_rowblock_factor": ([_vp, _int, _vp, _i64, _vp, _vp], _int),
     "ld_rowblock_update": ([_vp, _int, _i64, _i64, _i64, _vp, _vp, _vp, _vp], _int),
     "ld_profile_start": ([ctypes.c_char_p], _int),
@@ -174,6 +176,14 @@ def ld_rankb_update(mode, M, N, K, A, lda, B, ldb, D, ldd, stream) -> int:
 
 def ld_logdet_noalloc(A, a_dtype, n, lda, stream, sign, logabs) -> int:
     return load().ld_logdet_noalloc(A, a_dtype, n, lda, stream, sign, logabs)
+
+
+def ld_logdet_sparse(row_ptr, col_idx, vals, v_dtype, n, mode, stream, sign, logabs) -> int:
+    return load().ld_logdet_sparse(row_ptr, col_idx, vals, v_dtype, n, mode, stream, sign, logabs)
+
+
+def ld_sparse_blocks(row_ptr, col_idx, n, col_of_row, block_of_row, nblocks) -> int:
+    return load().ld_sparse_blocks(row_ptr, col_idx, n, col_of_row, block_of_row, nblocks)
 
 
 def ld_profile_start(kernel=None) -> int:

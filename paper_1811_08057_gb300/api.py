@@ -291,3 +291,46 @@ class LogAbsDet(torch.autograd.Function):
 def logabsdet(A: torch.Tensor, mode="f32_plain") -> torch.Tensor:
     """Differentiable log|det A| (n x n or B x n x n) through liblogdet."""
     return LogAbsDet.apply(A, mode)
+
+
+def _csr_arrays(row_ptr: torch.Tensor, col_idx: torch.Tensor):
+    if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int64:
+        raise TypeError("row_ptr and col_idx must be int64 tensors")
+    if row_ptr.dim() != 1 or col_idx.dim() != 1:
+        raise ValueError("row_ptr and col_idx must be 1-D")
+    return row_ptr.contiguous(), col_idx.contiguous()
+
+
+def logdet_sparse(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor,
+                  mode="f64_plain", stream=None):
+    """(sign, log|det A|) of a CSR matrix as 0-d FP64 CUDA tensors: the diagonal
+    blocks of its block triangular form condensed on the GPU (ld_logdet_sparse).
+    The arrays may live on the host or on the GPU; the call waits for the stream."""
+    row_ptr, col_idx = _csr_arrays(row_ptr, col_idx)
+    vals = vals.contiguous()
+    n = row_ptr.numel() - 1
+    if n < 0:
+        raise ValueError("row_ptr needs n + 1 entries")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    code = _lib.ld_logdet_sparse(row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr(),
+                                 _dtype_code(vals), n, _mode_code(mode), _stream_handle(stream),
+                                 out.data_ptr(), out.data_ptr() + 8)
+    _lib.check("ld_logdet_sparse", code)
+    return out[0], out[1]
+
+
+def sparse_blocks(row_ptr: torch.Tensor, col_idx: torch.Tensor):
+    """The structure analysis of logdet_sparse on the host: (col_of_row,
+    block_of_row, nblocks) as CPU tensors and an int; nblocks = -1 when the matrix
+    has no complete transversal (structurally singular)."""
+    import ctypes
+    row_ptr, col_idx = _csr_arrays(row_ptr.cpu(), col_idx.cpu())
+    n = row_ptr.numel() - 1
+    cor = torch.empty(max(n, 0), dtype=torch.int64)
+    blk = torch.empty(max(n, 0), dtype=torch.int64)
+    nb = ctypes.c_int64()
+    code = _lib.ld_sparse_blocks(row_ptr.data_ptr(), col_idx.data_ptr(), n, cor.data_ptr(),
+                                 blk.data_ptr(), ctypes.addressof(nb))
+    _lib.check("ld_sparse_blocks", code)
+    return cor, blk, nb.value
+

@@ -18,6 +18,12 @@ stated distribution; these recipes stand in for its matrices):
   dyadic_lu(n, seed)             integer/dyadic matrices whose whole condensation
                                  sweep is exact in FP32, with the pivot labels and
                                  determinant known by construction
+  sparse_block_triangular(sizes, seed, ...)
+                                 a CSR matrix whose rows and columns are randomly
+                                 permuted from a block upper triangular matrix
+                                 with irreducible diagonal blocks of the given
+                                 sizes (stands in for the sparse matrices the
+                                 paper leaves to future work)
 """
 from __future__ import annotations
 
@@ -271,3 +277,85 @@ def spd_reflectors_torch(N: int, seed: int, lo: float, hi: float, device, k: int
     if dtype is not None:
         A = A.to(dtype)
     return A, sum_log
+
+
+def sparse_block_triangular(sizes, seed: int, off_density: float = 0.002, diag_shift: float = 2.0,
+                            integer: bool = False, dense: bool = True, symmetric: bool = False):
+    """CSR arrays (row_ptr, col_idx, vals) and the dense matrix of a sparse n x n
+    matrix, n = sum(sizes): block upper triangular with diagonal blocks of the
+    given sizes, rows and columns then permuted at random.
+
+    Diagonal block of size s: its diagonal, a cyclic superdiagonal (entry (i,
+    i+1 mod s)), which makes the block irreducible, and iid entries at density
+    min(1, 8/s) with values N(0, 1/s); the diagonal adds diag_shift. Entries above
+    the diagonal blocks at density off_density. integer=True draws small integers
+    instead (diagonal +-2, others in {-1, 1}). Column indices are sorted within a
+    row; the stored values are FP64. dense=False returns None for the dense
+    matrix (large n). symmetric=True permutes rows and columns alike, so the
+    diagonal stays stored."""
+    rng = np.random.default_rng(seed)
+    sizes = [int(x) for x in sizes]
+    n = int(sum(sizes))
+    starts = np.cumsum([0] + sizes[:-1])
+    rows, cols, vals = [], [], []
+
+    def draw(k):
+        if integer:
+            return rng.choice([-1.0, 1.0], size=k)
+        return rng.standard_normal(k)
+
+    for b, s0 in zip(sizes, starts):
+        idx = np.arange(b)
+        # diagonal, cyclic superdiagonal, random interior
+        r = [idx, idx] if b > 1 else [idx]
+        c = [idx, (idx + 1) % b] if b > 1 else [idx]
+        dens = min(1.0, 8.0 / b)
+        mask = rng.random((b, b)) < dens
+        ri, ci = np.nonzero(mask)
+        keep = (ri != ci) & (ci != (ri + 1) % b)
+        r.append(ri[keep])
+        c.append(ci[keep])
+        rr = np.concatenate(r) + s0
+        cc = np.concatenate(c) + s0
+        v = draw(len(rr))
+        if not integer:
+            v = v / math.sqrt(b)
+        d = rr == cc
+        v[d] = (rng.choice([-1.0, 1.0], size=int(d.sum())) * 2.0 if integer
+                else v[d] + diag_shift)
+        rows.append(rr)
+        cols.append(cc)
+        vals.append(v)
+    # entries above the diagonal blocks
+    blk = np.repeat(np.arange(len(sizes)), sizes)
+    m = int(off_density * n * n)
+    if m > 0 and len(sizes) > 1:
+        ri = rng.integers(0, n, size=m)
+        ci = rng.integers(0, n, size=m)
+        keep = blk[ri] < blk[ci]
+        rows.append(ri[keep])
+        cols.append(ci[keep])
+        vals.append(draw(int(keep.sum())))
+    R = np.concatenate(rows)
+    C = np.concatenate(cols)
+    V = np.concatenate(vals)
+    # one entry per position (the first drawn wins)
+    key = R * n + C
+    _, first = np.unique(key, return_index=True)
+    R, C, V = R[first], C[first], V[first]
+    # random row and column permutations
+    pr = rng.permutation(n)
+    pc = pr if symmetric else rng.permutation(n)
+    R = pr[R]
+    C = pc[C]
+    order = np.lexsort((C, R))
+    R, C, V = R[order], C[order], V[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, R + 1, 1)
+    row_ptr = np.cumsum(row_ptr).astype(np.int64)
+    full = None
+    if dense:
+        full = np.zeros((n, n))
+        full[R, C] = V
+    return row_ptr, C.astype(np.int64), V.astype(np.float64), full
+
