@@ -349,6 +349,8 @@ extern "C" ld_status ld_logdet_sparse(const int64_t* row_ptr, const int64_t* col
   const int64_t* rp = row_ptr;
   const int64_t* ci = col_idx;
   const bool rp_dev = is_device_pointer(row_ptr), ci_dev = is_device_pointer(col_idx);
+  // device arrays may still be written by work queued on the caller's stream
+  if ((rp_dev || ci_dev) && cudaStreamSynchronize(stream) != cudaSuccess) return LD_ERR_CUDA;
   if (rp_dev) {
     rp_h.resize(n + 1);
     if (cudaMemcpy(rp_h.data(), row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
