@@ -149,3 +149,21 @@ def test_sign_of_a_permutation_matrix():
     cor, blk, nb = analyse(rp, ci)
     assert np.array_equal(cor, perm) and nb == n
     assert oracle.logdet(D).sign in (1.0, -1.0) and math.isfinite(oracle.logdet(D).logabs)
+
+
+def test_small_edge_structures():
+    # 1 x 1: one block; with no entry: structurally singular
+    assert analyse(np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int64))[2] == 1
+    assert analyse(np.array([0, 0], dtype=np.int64), np.zeros(0, dtype=np.int64))[2] == -1
+    # a dense matrix is one irreducible block
+    D = np.ones((6, 6))
+    rp, ci, v = csr_of(D)
+    cor, blk, nb = analyse(rp, ci)
+    assert nb == 1 and np.array_equal(cor, np.arange(6))
+    # upper triangular with a full diagonal: n blocks of one, in an order in
+    # which every stored entry goes to a lower or equal block number
+    U = np.triu(np.ones((7, 7)))
+    rp, ci, v = csr_of(U)
+    cor, blk, nb = analyse(rp, ci)
+    assert nb == 7
+    check_structure(rp, ci, cor, blk, nb)
