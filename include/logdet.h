@@ -335,7 +335,8 @@ ld_status ld_logdet_noalloc(const void* A, ld_dtype a_dtype, int64_t n, int64_t 
  * blocks do not enter the result (as in exact arithmetic), so a NaN or an
  * infinity there is not propagated. The call waits for `stream` before it
  * returns (the structure analysis needs the host).
- * Errors: LD_ERR_INVALID_ARG for n < 0, NULL arrays (n > 0), a malformed
+ * Errors: LD_ERR_INVALID_ARG for n < 0, a NULL row_ptr (n > 0), NULL col_idx or
+ * vals with stored entries (they may be NULL when row_ptr[n] = 0), a malformed
  * structure (row_ptr[0] != 0, decreasing offsets, a column out of range or
  * repeated in a row) or an unknown enum; LD_ERR_ALLOC / LD_ERR_CUDA as named;
  * the errors of ld_logdet / ld_logdet_batched for the blocks.

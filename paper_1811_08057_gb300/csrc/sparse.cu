@@ -298,12 +298,13 @@ extern "C" ld_status ld_sparse_blocks(const int64_t* row_ptr, const int64_t* col
                                       int64_t* col_of_row, int64_t* block_of_row,
                                       int64_t* nblocks) {
   using namespace ld;
-  if (n < 0 || !nblocks || (n > 0 && (!row_ptr || !col_idx || !col_of_row || !block_of_row)))
+  if (n < 0 || !nblocks || (n > 0 && (!row_ptr || !col_of_row || !block_of_row)))
     return LD_ERR_INVALID_ARG;
   if (n == 0) {
     *nblocks = 0;
     return LD_OK;
   }
+  if (row_ptr[n] > 0 && !col_idx) return LD_ERR_INVALID_ARG;  // NULL only without entries
   std::vector<int64_t> cor, roc, comp;
   int64_t nc = 0;
   bool singular = false;
@@ -324,8 +325,7 @@ extern "C" ld_status ld_logdet_sparse(const int64_t* row_ptr, const int64_t* col
                                       void* stream_v, double* sign, double* logabs) {
   using namespace ld;
   if (n < 0 || !sign || !logabs || !mode_valid(mode) ||
-      (v_dtype != LD_DTYPE_F64 && v_dtype != LD_DTYPE_F32) ||
-      (n > 0 && (!row_ptr || !col_idx)))
+      (v_dtype != LD_DTYPE_F64 && v_dtype != LD_DTYPE_F32) || (n > 0 && !row_ptr))
     return LD_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const bool sign_dev = is_device_pointer(sign), log_dev = is_device_pointer(logabs);
@@ -358,7 +358,7 @@ extern "C" ld_status ld_logdet_sparse(const int64_t* row_ptr, const int64_t* col
     rp = rp_h.data();
   }
   const int64_t nnz = rp[n];
-  if (nnz < 0 || (nnz > 0 && !vals)) return LD_ERR_INVALID_ARG;
+  if (nnz < 0 || (nnz > 0 && (!vals || !col_idx))) return LD_ERR_INVALID_ARG;
   if (ci_dev) {
     ci_h.resize(std::max<int64_t>(nnz, 1));
     if (nnz > 0 &&

@@ -104,6 +104,9 @@ def test_small_integer_matrices_exact(seed):
 
 
 def test_singular_cases():
+    # no stored entry at all (empty column and value arrays)
+    z = np.zeros(0, dtype=np.int64)
+    assert run(np.zeros(4, dtype=np.int64), z, np.zeros(0), "f64_plain") == (0.0, -math.inf)
     # no complete transversal: det A = 0 for every value of the entries
     D = np.array([[1.0, 0, 0], [2.0, 0, 0], [1.0, 1.0, 1.0]])
     R, C = np.nonzero(D)
